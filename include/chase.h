@@ -1,0 +1,195 @@
+/*
+ * chase.h -- C ABI of a single-GPU (sm_103a) Chebyshev-filtered subspace
+ * eigensolver for the lowest eigenpairs of a dense complex Hermitian matrix,
+ * after Wu & Di Napoli, "Advancing the distributed Multi-GPU ChASE library
+ * through algorithm optimization and NCCL library" (arXiv 2309.15595).
+ *
+ * Problem (Section 1): A x = lambda x with A^H = A in C^{N x N}; the nev lowest
+ * eigenpairs are wanted and nex extra vectors widen the search space
+ * (Alg. 2 "Require"/"Ensure").
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are complex128, interleaved (re, im), COLUMN-MAJOR (LAPACK):
+ *     element (i, j) of A lives at A[i + j * lda]. Leading dimensions must be
+ *     >= the number of rows. A must hold the full Hermitian matrix (both
+ *     triangles); a row-major Hermitian buffer read column-major is conj(A).
+ *   - Pointers named A, V, ritz, resid are DEVICE pointers owned by the caller.
+ *     Pointers documented as host arrays are host memory.
+ *   - All work is enqueued on the stream given to chase_create, in order.
+ *     Calls that need a host decision (chase_qr, chase_solve, chase_lanczos,
+ *     chase_rayleigh_ritz) synchronise that stream before returning; the others
+ *     return after enqueueing.
+ *   - The library allocates all of its workspace in chase_create and frees it in
+ *     chase_destroy; no other call allocates device memory.
+ *   - Every call returns a chase_status. On CHASE_ERR_INVALID_ARG nothing was
+ *     enqueued. On CHASE_ERR_CUDA the context should be destroyed.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef CHASE_GB300_H
+#define CHASE_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CHASE_API __attribute__((visibility("default")))
+#else
+#define CHASE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum chase_status {
+  CHASE_OK = 0,
+  CHASE_ERR_INVALID_ARG = 1,   /* bad size, pointer, degree or parameter */
+  CHASE_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  CHASE_ERR_OOM = 3,           /* workspace allocation failed in chase_create */
+  CHASE_ERR_QR_BREAKDOWN = 4,  /* every CholeskyQR variant and the fallback failed */
+  CHASE_ERR_HEEV_NOCONV = 5,   /* Jacobi sweep cap reached before convergence */
+  CHASE_ERR_NOT_CONVERGED = 6  /* max_iter reached; outputs hold the best pairs */
+} chase_status;
+
+/* Filter arithmetic (the QR, Rayleigh-Ritz, residual and Lanczos steps are
+ * always FP64). */
+enum {
+  CHASE_FP64 = 0,          /* filter HEMM in FP64 (DFMA) */
+  CHASE_MIXED_BF16X3 = 1   /* filter in split-BF16 x3 on tensor cores (FP32
+                              accumulation) while the residuals are above
+                              switch_tol, FP64 afterwards */
+};
+
+/* QR variant codes (Alg. 4). */
+enum {
+  CHASE_QR_CHOLQR1 = 1,
+  CHASE_QR_CHOLQR2 = 2,
+  CHASE_QR_SHIFTED = 3,   /* shifted CholeskyQR pass + CholeskyQR2 */
+  CHASE_QR_FALLBACK = 4   /* POTRF failed inside the shifted branch: repeated
+                             shifted passes, then CholeskyQR2 */
+};
+
+typedef struct chase_c128 { double re, im; } chase_c128;
+
+typedef struct chase_params {
+  int64_t N;              /* matrix order, >= 2 */
+  int64_t nev;            /* wanted eigenpairs, >= 1 */
+  int64_t nex;            /* extra search vectors, >= 0; nev + nex <= N */
+  int32_t deg_init;       /* first-iteration filter degree (20, Section 4.2), even */
+  int32_t deg_max;        /* degree cap (36, Section 4.2) */
+  int32_t deg_extra;      /* safety margin added by degreeOpt (2) */
+  int32_t deg_opt;        /* 1: per-vector degree optimisation (Alg. 2 "opt") */
+  int32_t max_iter;       /* MaxIter of Alg. 2 */
+  int32_t lanczos_steps;  /* Lanczos steps per run (25), <= N */
+  int32_t lanczos_vecs;   /* Lanczos runs (4), 1..8 */
+  int32_t precision;      /* CHASE_FP64 or CHASE_MIXED_BF16X3 */
+  int32_t scaled_filter;  /* 1: filter normalised at mu_1 (default); 0: plain
+                             T_m((A - cI)/e) recurrence */
+  int32_t reserved;
+  double tol;             /* residual tolerance relative to ||A|| (1e-10, Section 4) */
+  double switch_tol;      /* mixed -> FP64 switch, relative residual (1e-5) */
+} chase_params;
+
+typedef struct chase_stats {
+  int32_t iters;          /* outer iterations done */
+  int32_t locked;         /* converged (locked) pairs */
+  int64_t matvecs;        /* sum of filter degrees over filtered columns */
+  int64_t matvecs_mixed;  /* of which filtered in reduced precision */
+  double b_sup, mu_1, mu_ne, norm_est;   /* Lanczos bounds and ||A|| estimate */
+  double ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid, ms_total;
+  double filter_flops;    /* 8 N^2 per MatVec */
+  int32_t qr_variant_count[5];  /* index = CHASE_QR_* */
+  int32_t switch_iter;    /* iteration at which the filter became FP64 (0: never mixed) */
+} chase_stats;
+
+/* Fills *p with the defaults above for the given sizes. Host only. */
+CHASE_API void chase_default_params(chase_params* p, int64_t N, int64_t nev, int64_t nex);
+
+/* Creates a context: validates *p and allocates every workspace buffer for
+ * order N and nev + nex vectors on the current CUDA device. stream may be NULL
+ * (legacy default stream). Returns CHASE_ERR_OOM if allocation fails. */
+CHASE_API int chase_create(const chase_params* p, void* stream, struct chase_ctx** out);
+
+/* Frees the workspace and the context. Safe on NULL. */
+CHASE_API int chase_destroy(struct chase_ctx* ctx);
+
+/* Full solve, Alg. 2 on one GPU (the 2D grid collapses to one block):
+ * Lanczos bounds, then {degreeOpt + sort, Filter, CondEst, 1D-CAQR, restore
+ * locked, Rayleigh-Ritz, Residual, Locking} until nev pairs are locked or
+ * max_iter is reached.
+ *   A      device, N x N, lda >= N, read only.
+ *   V      device, N x (nev+nex), ldv >= N: in = start block (need not be
+ *          orthonormal), out = Ritz vectors; columns 0..nev-1 are the answer,
+ *          ascending.
+ *   lanczos_start  device, N x lanczos_vecs, ld = ldl; may be NULL, then the
+ *          first lanczos_vecs columns of the input V start the Lanczos runs.
+ *   ritz, resid  device, nev+nex doubles: Ritz values (ascending in 0..nev-1)
+ *          and absolute residual norms ||A v - theta v||_2.
+ *   stats  host, may be NULL.
+ * Returns CHASE_ERR_NOT_CONVERGED if max_iter was reached (outputs are then the
+ * current best pairs). */
+CHASE_API int chase_solve(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                chase_c128* V, int64_t ldv, const chase_c128* lanczos_start,
+                int64_t ldl, double* ritz, double* resid, chase_stats* stats);
+
+/* Spectral bounds by Lanczos (Alg. 1 "Lanczos", Alg. 2 first line): runs
+ * nvec (<= lanczos_vecs) Lanczos recurrences of lanczos_steps steps from the
+ * columns of Q0 (device, N x nvec, ldq >= N) and writes, to the HOST array
+ * bounds[4]: b_sup, mu_1, mu_ne, norm_est (see the design notes for the DoS
+ * reading). Synchronises. */
+CHASE_API int chase_lanczos(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                  const chase_c128* Q0, int64_t ldq, int64_t nvec, double* bounds);
+
+/* Chebyshev filter, Eq. 1 with gamma_i = c, in place on V[:, 0:ncols]:
+ * column j becomes p_{degs[j]}(A) v_j with p_m normalised at mu_1 (or plain
+ * T_m((A-cI)/e) if scaled_filter = 0). degs is a HOST array of ncols EVEN
+ * degrees >= 2, sorted ascending (Section 3.1 even-degree rule; Alg. 1 sort).
+ * precision: CHASE_FP64 or CHASE_MIXED_BF16X3 (the latter needs a context
+ * created with that precision). Requires e > 0 and mu_1 <= c - e, so that
+ * the normalisation T_m((mu_1 - c)/e) never vanishes. */
+CHASE_API int chase_filter(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                 chase_c128* V, int64_t ldv, int64_t ncols, const int32_t* degs,
+                 double c, double e, double mu_1, int32_t precision);
+
+/* 1D-CAQR of Alg. 4 on V[:, 0:ncols] (ncols <= nev+nex), in place: V becomes
+ * Q with V_in = Q R, R upper triangular with positive real diagonal. The
+ * variant follows cond_est (> 1e8 shifted, < 20 CholeskyQR1, else
+ * CholeskyQR2); *variant_used (host, may be NULL) receives a CHASE_QR_* code.
+ * Synchronises (POTRF info is a host decision). */
+CHASE_API int chase_qr(struct chase_ctx* ctx, chase_c128* V, int64_t ldv, int64_t ncols,
+             double cond_est, int32_t* variant_used);
+
+/* Rayleigh-Ritz (Alg. 2 RR lines): with Q = V[:, 0:ncols] orthonormal, forms
+ * G = Q^H A Q, diagonalises it with a two-sided Jacobi method and overwrites V
+ * with the Ritz vectors Q Y; ritz (device, ncols doubles) receives the Ritz
+ * values ascending. Synchronises. */
+CHASE_API int chase_rayleigh_ritz(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                        chase_c128* V, int64_t ldv, int64_t ncols, double* ritz);
+
+/* Residual norms (Alg. 2 residual lines): resid[j] = ||A v_j - ritz[j] v_j||_2
+ * for j < ncols. V, ritz, resid are device arrays. */
+CHASE_API int chase_residuals(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                    const chase_c128* V, int64_t ldv, const double* ritz,
+                    int64_t ncols, double* resid);
+
+/* Alg. 5 condition estimate, host arithmetic on host arrays in the solver's
+ * current column order: t' = (ritz[0]-c)/e, t = (ritz[locked]-c)/e,
+ * cond = |rho(t)|^d |rho(t')|^(d_M - d), d = degs[locked],
+ * d_M = max(degs[locked:n]). */
+CHASE_API double chase_cond_est(const double* ritz, const int32_t* degs, int64_t n,
+                      int64_t locked, double c, double e);
+
+/* degreeOpt (host arithmetic, host arrays): for j < n,
+ * degs[j] = even clamp of ceil(ln(resid[j]/tol_abs)/ln rho_j) + deg_extra
+ * with rho_j = |t_j| + sqrt(t_j^2 - 1), t_j = (ritz[j]-c)/e. */
+CHASE_API void chase_degree_opt(const double* resid, const double* ritz, int64_t n,
+                      double c, double e, double tol_abs, int32_t deg_max,
+                      int32_t deg_extra, int32_t* degs);
+
+/* Human-readable name of a chase_status. */
+CHASE_API const char* chase_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHASE_GB300_H */

@@ -150,10 +150,14 @@ def chebyshev_filter(A, V, degs, c, e, mu_1, scaled=True):
 
 # ------------------------------------------------------------------- CondEst
 def _rho(t: float) -> float:
-    """|rho| = max{|t - sqrt(t^2-1)|, |t + sqrt(t^2-1)|} (Alg. 5), with the
-    complex square root for |t| < 1 (both roots then have modulus 1)."""
-    s = np.sqrt(complex(t * t - 1.0))
-    return float(max(abs(t - s), abs(t + s)))
+    """|rho| = max{|t - sqrt(t^2-1)|, |t + sqrt(t^2-1)|} (Alg. 5). For |t| < 1
+    the square root is imaginary and both roots t +- i sqrt(1-t^2) have
+    modulus exactly 1."""
+    d = t * t - 1.0
+    if d < 0.0:
+        return 1.0
+    s = math.sqrt(d)
+    return max(abs(t - s), abs(t + s))
 
 
 def cond_est(ritz, c, e, degs, locked):

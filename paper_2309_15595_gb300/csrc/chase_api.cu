@@ -1,0 +1,629 @@
+// C ABI and host driver of the single-GPU ChASE solver (Alg. 2 on one GPU).
+//
+// The host code only makes the scalar decisions the paper leaves to the
+// driver (degrees, sort order, QR variant, locking, precision switch) on
+// arrays of nev + nex doubles; every vector and matrix operation runs in the
+// kernels of this library on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "mixed.cuh"
+
+using namespace chase;
+
+struct chase_ctx {
+  chase_params p;
+  cudaStream_t stream;
+  int64_t N, ne;
+  double2* V2 = nullptr;        // N x ne, ld N  (C2 of Alg. 2)
+  double2* W = nullptr;         // N x ne, ld N  (B of Alg. 2, filter ping-pong)
+  double2* G = nullptr;         // ne x ne, ld ne
+  double2* Yeig = nullptr;      // ne x ne, ld ne
+  double2* gram_ws = nullptr;
+  size_t gram_ws_elems = 0;
+  double2* dinv = nullptr;
+  int* info = nullptr;
+  double* resid_partial = nullptr;
+  double* dscal = nullptr;
+  int* perm_d = nullptr;
+  double* host = nullptr;       // pinned: 2 ne + 16 doubles
+  JacobiWork jw{};
+  LanczosWork lw{};
+  MixedWork mw{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+const double kU = 1.1102230246251565e-16;  // 2^-53
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    fprintf(stderr, "[chase] CUDA error in %s: %s\n", what, cudaGetErrorString(e));
+    return CHASE_ERR_CUDA;
+  }
+  return CHASE_OK;
+}
+#define CK(call)                                              \
+  do {                                                        \
+    int _rc = cuda_fail((call), #call);                       \
+    if (_rc != CHASE_OK) return _rc;                          \
+  } while (0)
+#define RC(call)                                              \
+  do {                                                        \
+    int _rc = (call);                                         \
+    if (_rc != CHASE_OK) return _rc;                          \
+  } while (0)
+
+double rho_of(double t) {
+  // max{|t - sqrt(t^2-1)|, |t + sqrt(t^2-1)|}: |t| + sqrt(t^2-1) outside
+  // [-1, 1], exactly 1 inside (complex conjugate roots on the unit circle).
+  const double d = t * t - 1.0;
+  if (d < 0.0) return 1.0;
+  const double s = std::sqrt(d);
+  return std::max(std::fabs(t - s), std::fabs(t + s));
+}
+
+struct PhaseTimer {
+  cudaStream_t s;
+  cudaEvent_t a, b;
+  double* acc;
+  PhaseTimer(chase_ctx* c, double* acc_) : s(c->stream), a(c->ev0), b(c->ev1), acc(acc_) {
+    if (acc) cudaEventRecord(a, s);
+  }
+  void stop() {
+    if (!acc) return;
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    *acc += ms;
+    acc = nullptr;
+  }
+  ~PhaseTimer() { stop(); }
+};
+
+void free_ctx(chase_ctx* c) {
+  if (!c) return;
+  void* bufs[] = {c->V2, c->W, c->G, c->Yeig, c->gram_ws, c->dinv, c->info, c->resid_partial,
+                  c->dscal, c->perm_d, c->jw.Gw, c->jw.Zw, c->jw.params, c->jw.red,
+                  c->lw.Q, c->lw.ws, c->lw.red, c->lw.ab, c->lw.T, c->lw.theta, c->lw.Z,
+                  c->lw.out4, c->lw.status};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  mixed_free(c->mw);
+  if (c->host) cudaFreeHost(c->host);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+int validate_params(const chase_params* p) {
+  if (!p) return CHASE_ERR_INVALID_ARG;
+  if (p->N < 2 || p->nev < 1 || p->nex < 0 || p->nev + p->nex > p->N) return CHASE_ERR_INVALID_ARG;
+  if (p->deg_init < 2 || (p->deg_init & 1) || p->deg_max < 2 || p->deg_extra < 0)
+    return CHASE_ERR_INVALID_ARG;
+  if (p->max_iter < 1 || !(p->tol > 0.0) || !(p->switch_tol > 0.0)) return CHASE_ERR_INVALID_ARG;
+  if (p->lanczos_steps < 1 || p->lanczos_steps > 64 || p->lanczos_steps > p->N)
+    return CHASE_ERR_INVALID_ARG;
+  if (p->lanczos_vecs < 1 || p->lanczos_vecs > 8) return CHASE_ERR_INVALID_ARG;
+  if (p->precision != CHASE_FP64 && p->precision != CHASE_MIXED_BF16X3) return CHASE_ERR_INVALID_ARG;
+  return CHASE_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+// ------------------------------------------------------------------ filter
+int filter_impl(chase_ctx* c, const double2* A, int64_t lda, double2* V, int64_t ldv,
+                int64_t ncols, const int32_t* degs, double cc, double e, double mu1, int prec,
+                double* ms) {
+  if (ncols == 0) return CHASE_OK;
+  const int dmax = degs[ncols - 1];
+  // Eq. 1 coefficients (gamma_i = c), see chase_filter in chase.h
+  std::vector<double> al(dmax + 1, 0.0), be(dmax + 1, 0.0);
+  if (c->p.scaled_filter) {
+    const double sigma1 = e / (mu1 - cc);
+    al[1] = sigma1 / e;
+    double sig = sigma1;
+    for (int i = 2; i <= dmax; ++i) {
+      const double sn = 1.0 / (2.0 / sigma1 - sig);
+      al[i] = 2.0 * sn / e;
+      be[i] = -sig * sn;
+      sig = sn;
+    }
+  } else {
+    al[1] = 1.0 / e;
+    for (int i = 2; i <= dmax; ++i) {
+      al[i] = 2.0 / e;
+      be[i] = -1.0;
+    }
+  }
+  PhaseTimer tm(c, ms);
+  if (prec == CHASE_MIXED_BF16X3)
+    return mixed_filter(c->stream, c->N, A, lda, V, ldv, ncols, degs, cc, al.data(), be.data(),
+                        c->W, c->N, c->mw);
+  double2* buf[2] = {V, c->W};
+  const int64_t ld[2] = {ldv, c->N};
+  for (int i = 1; i <= dmax; ++i) {
+    const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
+    const int64_t nact = ncols - j0;
+    const int s = (i - 1) & 1, d = i & 1;
+    Epilogue ep{};
+    ep.mode = EPI_FILTER;
+    ep.alpha = al[i];
+    ep.beta = (i == 1) ? 0.0 : be[i];
+    ep.gamma = cc;
+    ep.X = buf[s] + j0 * ld[s];
+    ep.ldx = ld[s];
+    ep.Y = buf[d] + j0 * ld[d];
+    ep.ldy = ld[d];
+    CK(zgemm_nn(c->stream, c->N, nact, c->N, A, lda, buf[s] + j0 * ld[s], ld[s], ep));
+  }
+  return CHASE_OK;
+}
+
+int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
+  for (int64_t j = 0; j < n; ++j) {
+    if (degs[j] < 2 || (degs[j] & 1) || degs[j] > deg_cap) return CHASE_ERR_INVALID_ARG;
+    if (j > 0 && degs[j] < degs[j - 1]) return CHASE_ERR_INVALID_ARG;
+  }
+  return CHASE_OK;
+}
+
+// ---------------------------------------------------------------------- QR
+// One CholeskyQR pass (Alg. 3 body): G = X^H X (+ s I), G = U^H U, X = X U^-1.
+// Returns the POTRF info through *info_h (0 = success; X untouched otherwise).
+int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
+                int* info_h) {
+  CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
+           c->gram_ws_elems));
+  if (shift_factor > 0.0) CK(add_trace_shift(c->stream, n, c->G, c->ne, shift_factor, c->dscal));
+  CK(potrf_upper(c->stream, n, c->G, c->ne, c->dinv, c->info));
+  CK(trsm_right_upper(c->stream, c->N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
+  CK(cudaMemcpyAsync(info_h, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return CHASE_OK;
+}
+
+int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32_t* variant) {
+  int* info_h = reinterpret_cast<int*>(c->host + 2 * c->ne + 8);
+  int v = cond > 1e8 ? CHASE_QR_SHIFTED : (cond < 20 ? CHASE_QR_CHOLQR1 : CHASE_QR_CHOLQR2);
+  if (v != CHASE_QR_SHIFTED) {
+    const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
+    bool ok = true;
+    for (int k = 0; k < passes && ok; ++k) {
+      RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
+      ok = (*info_h == 0);
+    }
+    if (ok) {
+      if (variant) *variant = v;
+      return CHASE_OK;
+    }
+    v = CHASE_QR_SHIFTED;  // reading: a failed CholeskyQR1/2 re-runs the shifted branch
+  }
+  // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2
+  const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    RC(cholqr_pass(c, X, ldx, n, factor, info_h));
+    if (*info_h != 0) return CHASE_ERR_QR_BREAKDOWN;
+    RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
+    if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
+    if (*info_h == 0) {
+      if (variant) *variant = attempt == 0 ? CHASE_QR_SHIFTED : CHASE_QR_FALLBACK;
+      return CHASE_OK;
+    }
+  }
+  return CHASE_ERR_QR_BREAKDOWN;
+}
+
+// ----------------------------------------------------------- Rayleigh-Ritz
+// Q (N x n, ldq) orthonormal, not aliasing V. V[:, 0:n] = Q Y, ritz = eigenvalues.
+int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64_t ldq,
+            double2* V, int64_t ldv, int64_t n, double* ritz) {
+  Epilogue ep{};
+  ep.mode = EPI_STORE;
+  ep.Y = c->W;
+  ep.ldy = c->N;
+  CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, Q, ldq, ep));                    // W = A Q
+  CK(zgram(c->stream, c->N, n, n, Q, ldq, c->W, c->N, c->G, c->ne, false, c->gram_ws,
+           c->gram_ws_elems));                                                   // G = Q^H W
+  CK(hermitian_part(c->stream, n, c->G, c->ne));
+  int sweeps = 0;
+  RC(jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps));
+  Epilogue e2{};
+  e2.mode = EPI_STORE;
+  e2.Y = V;
+  e2.ldy = ldv;
+  CK(zgemm_nn(c->stream, c->N, n, n, Q, ldq, c->Yeig, c->ne, e2));               // V = Q Y
+  return CHASE_OK;
+}
+
+int resid_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* V, int64_t ldv,
+               const double* ritz, int64_t n, double* resid) {
+  if (n == 0) return CHASE_OK;
+  Epilogue ep{};
+  ep.mode = EPI_RESID;
+  ep.X = V;
+  ep.ldx = ldv;
+  ep.theta = ritz;
+  ep.partial = c->resid_partial;
+  CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, V, ldv, ep));
+  CK(resid_reduce(c->stream, c->resid_partial, zgemm_row_tiles(c->N), n, resid));
+  return CHASE_OK;
+}
+
+int lanczos_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q0, int64_t ldq,
+                 int nvec, double* out4_h) {
+  CK(lanczos_bounds(c->stream, c->N, A, lda, Q0, ldq, nvec, c->p.lanczos_steps, c->ne, c->lw));
+  CK(cudaMemcpyAsync(out4_h, c->lw.out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->lw.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return st ? CHASE_ERR_HEEV_NOCONV : CHASE_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void chase_default_params(chase_params* p, int64_t N, int64_t nev, int64_t nex) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->N = N;
+  p->nev = nev;
+  p->nex = nex;
+  p->deg_init = 20;
+  p->deg_max = 36;
+  p->deg_extra = 2;
+  p->deg_opt = 1;
+  p->max_iter = 30;
+  p->lanczos_steps = (int32_t)std::min<int64_t>(25, N);
+  p->lanczos_vecs = 4;
+  p->precision = CHASE_FP64;
+  p->scaled_filter = 1;
+  p->tol = 1e-10;
+  p->switch_tol = 1e-5;
+}
+
+const char* chase_status_string(int s) {
+  switch (s) {
+    case CHASE_OK: return "CHASE_OK";
+    case CHASE_ERR_INVALID_ARG: return "CHASE_ERR_INVALID_ARG";
+    case CHASE_ERR_CUDA: return "CHASE_ERR_CUDA";
+    case CHASE_ERR_OOM: return "CHASE_ERR_OOM";
+    case CHASE_ERR_QR_BREAKDOWN: return "CHASE_ERR_QR_BREAKDOWN";
+    case CHASE_ERR_HEEV_NOCONV: return "CHASE_ERR_HEEV_NOCONV";
+    case CHASE_ERR_NOT_CONVERGED: return "CHASE_ERR_NOT_CONVERGED";
+    default: return "CHASE_UNKNOWN_STATUS";
+  }
+}
+
+double chase_cond_est(const double* ritz, const int32_t* degs, int64_t n, int64_t locked,
+                      double c, double e) {
+  if (!ritz || !degs || n <= 0 || locked < 0 || locked >= n || !(e > 0.0)) return NAN;
+  const double tp = (ritz[0] - c) / e;
+  const double t = (ritz[locked] - c) / e;
+  const double rho = rho_of(t), rhop = rho_of(tp);
+  const int d = degs[locked];
+  int dmax = d;
+  for (int64_t j = locked; j < n; ++j) dmax = std::max<int>(dmax, degs[j]);
+  return std::pow(rho, (double)d) * std::pow(rhop, (double)(dmax - d));
+}
+
+void chase_degree_opt(const double* resid, const double* ritz, int64_t n, double c, double e,
+                      double tol_abs, int32_t deg_max, int32_t deg_extra, int32_t* degs) {
+  const int dm = deg_max - (deg_max % 2);
+  for (int64_t j = 0; j < n; ++j) {
+    const double t = (ritz[j] - c) / e;
+    const double rho = rho_of(t);
+    int d;
+    if (rho <= 1.0) {
+      d = dm;
+    } else if (resid[j] <= tol_abs) {
+      d = 2;
+    } else {
+      const double x = (std::log(resid[j]) - std::log(tol_abs)) / std::log(rho);
+      d = x >= dm ? dm : (int)std::ceil(x) + deg_extra;
+    }
+    d = std::max(2, std::min(d, dm));
+    d += d % 2;
+    degs[j] = std::min(d, dm);
+  }
+}
+
+int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
+  if (!out) return CHASE_ERR_INVALID_ARG;
+  *out = nullptr;
+  RC(validate_params(p));
+  chase_ctx* c = new (std::nothrow) chase_ctx();
+  if (!c) return CHASE_ERR_OOM;
+  c->p = *p;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->N = p->N;
+  c->ne = p->nev + p->nex;
+  const int64_t N = c->N, ne = c->ne;
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dalloc(&c->V2, (size_t)N * ne));
+  A(dalloc(&c->W, (size_t)N * ne));
+  A(dalloc(&c->G, (size_t)ne * ne));
+  A(dalloc(&c->Yeig, (size_t)ne * ne));
+  c->gram_ws_elems = gram_workspace_elems(ne, ne);
+  A(dalloc(&c->gram_ws, c->gram_ws_elems));
+  A(dalloc(&c->dinv, (size_t)cdiv(ne, kNB) * kNB * kNB));
+  A(dalloc(&c->info, 4));
+  A(dalloc(&c->resid_partial, (size_t)zgemm_row_tiles(N) * ne));
+  A(dalloc(&c->dscal, 16));
+  A(dalloc(&c->perm_d, (size_t)ne));
+  A(dalloc(&c->jw.Gw, (size_t)ne * ne));
+  A(dalloc(&c->jw.Zw, (size_t)ne * ne));
+  A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
+  A(dalloc(&c->jw.red, 1024));
+  c->jw.nmax = ne;
+  A(dalloc(&c->lw.Q, (size_t)3 * N * 8));
+  A(dalloc(&c->lw.ws, skinny_workspace_elems(N, 8)));
+  A(dalloc(&c->lw.red, 2048));
+  A(dalloc(&c->lw.ab, 24 * 64));
+  A(dalloc(&c->lw.T, (size_t)8 * 64 * 64));
+  A(dalloc(&c->lw.theta, 8 * 64));
+  A(dalloc(&c->lw.Z, (size_t)8 * 64 * 64));
+  A(dalloc(&c->lw.out4, 4));
+  A(dalloc(&c->lw.status, 4));
+  if (ok && p->precision == CHASE_MIXED_BF16X3) A(mixed_alloc(c->mw, N, ne));
+  if (ok) A(cudaMallocHost(reinterpret_cast<void**>(&c->host), (2 * ne + 16) * sizeof(double)));
+  if (ok) A(cudaEventCreate(&c->ev0));
+  if (ok) A(cudaEventCreate(&c->ev1));
+  if (ok) A(cudaMemsetAsync(c->lw.status, 0, sizeof(int), c->stream));
+  if (ok) c->jw.host_red = c->host + 2 * ne + 12;
+  if (!ok) {
+    cudaGetLastError();
+    free_ctx(c);
+    return CHASE_ERR_OOM;
+  }
+  *out = c;
+  return CHASE_OK;
+}
+
+int chase_destroy(chase_ctx* ctx) {
+  if (ctx) {
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+  }
+  return CHASE_OK;
+}
+
+int chase_lanczos(chase_ctx* c, const chase_c128* A, int64_t lda, const chase_c128* Q0,
+                  int64_t ldq, int64_t nvec, double* bounds) {
+  if (!c || !A || !Q0 || !bounds || lda < c->N || ldq < c->N || nvec < 1 ||
+      nvec > c->p.lanczos_vecs)
+    return CHASE_ERR_INVALID_ARG;
+  return lanczos_impl(c, reinterpret_cast<const double2*>(A), lda,
+                      reinterpret_cast<const double2*>(Q0), ldq, (int)nvec, bounds);
+}
+
+int chase_filter(chase_ctx* c, const chase_c128* A, int64_t lda, chase_c128* V, int64_t ldv,
+                 int64_t ncols, const int32_t* degs, double cc, double e, double mu_1,
+                 int32_t precision) {
+  if (!c || !A || !V || lda < c->N || ldv < c->N || ncols < 0 || ncols > c->ne)
+    return CHASE_ERR_INVALID_ARG;
+  if (ncols > 0 && !degs) return CHASE_ERR_INVALID_ARG;
+  if (!(e > 0.0) || (c->p.scaled_filter && !(mu_1 <= cc - e))) return CHASE_ERR_INVALID_ARG;
+  if (precision != CHASE_FP64 && precision != CHASE_MIXED_BF16X3) return CHASE_ERR_INVALID_ARG;
+  if (precision == CHASE_MIXED_BF16X3 && c->p.precision != CHASE_MIXED_BF16X3)
+    return CHASE_ERR_INVALID_ARG;
+  RC(check_degs(degs, ncols, 1 << 20));
+  return filter_impl(c, reinterpret_cast<const double2*>(A), lda, reinterpret_cast<double2*>(V),
+                     ldv, ncols, degs, cc, e, mu_1, precision, nullptr);
+}
+
+int chase_qr(chase_ctx* c, chase_c128* V, int64_t ldv, int64_t ncols, double cond_est,
+             int32_t* variant_used) {
+  if (!c || !V || ldv < c->N || ncols < 1 || ncols > c->ne || std::isnan(cond_est))
+    return CHASE_ERR_INVALID_ARG;
+  return qr_impl(c, reinterpret_cast<double2*>(V), ldv, ncols, cond_est, variant_used);
+}
+
+int chase_rayleigh_ritz(chase_ctx* c, const chase_c128* A, int64_t lda, chase_c128* V,
+                        int64_t ldv, int64_t ncols, double* ritz) {
+  if (!c || !A || !V || !ritz || lda < c->N || ldv < c->N || ncols < 1 || ncols > c->ne)
+    return CHASE_ERR_INVALID_ARG;
+  double2* Vd = reinterpret_cast<double2*>(V);
+  CK(copy_cols(c->stream, c->N, ncols, Vd, ldv, c->V2, c->N));
+  RC(rr_impl(c, reinterpret_cast<const double2*>(A), lda, c->V2, c->N, Vd, ldv, ncols, ritz));
+  CK(cudaStreamSynchronize(c->stream));
+  return CHASE_OK;
+}
+
+int chase_residuals(chase_ctx* c, const chase_c128* A, int64_t lda, const chase_c128* V,
+                    int64_t ldv, const double* ritz, int64_t ncols, double* resid) {
+  if (!c || !A || !V || !ritz || !resid || lda < c->N || ldv < c->N || ncols < 0 ||
+      ncols > c->ne)
+    return CHASE_ERR_INVALID_ARG;
+  return resid_impl(c, reinterpret_cast<const double2*>(A), lda,
+                    reinterpret_cast<const double2*>(V), ldv, ritz, ncols, resid);
+}
+
+int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc, int64_t ldv,
+                const chase_c128* lanczos_start, int64_t ldl, double* ritz, double* resid,
+                chase_stats* stats) {
+  if (!c || !Ac || !Vc || !ritz || !resid || lda < c->N || ldv < c->N)
+    return CHASE_ERR_INVALID_ARG;
+  if (lanczos_start && ldl < c->N) return CHASE_ERR_INVALID_ARG;
+  if (!lanczos_start && c->p.lanczos_vecs > c->ne) return CHASE_ERR_INVALID_ARG;
+  const chase_params& P = c->p;
+  const int64_t N = c->N, ne = c->ne, nev = P.nev;
+  const double2* A = reinterpret_cast<const double2*>(Ac);
+  double2* C = reinterpret_cast<double2*>(Vc);
+  chase_stats st;
+  std::memset(&st, 0, sizeof(st));
+  cudaEvent_t t_start, t_end;
+  CK(cudaEventCreate(&t_start));
+  CK(cudaEventCreate(&t_end));
+  CK(cudaEventRecord(t_start, c->stream));
+
+  double b4[4];
+  {
+    PhaseTimer tm(c, &st.ms_lanczos);
+    const double2* Q0 = lanczos_start ? reinterpret_cast<const double2*>(lanczos_start) : C;
+    const int64_t ldq = lanczos_start ? ldl : ldv;
+    RC(lanczos_impl(c, A, lda, Q0, ldq, P.lanczos_vecs, b4));
+  }
+  const double b_sup = b4[0];
+  double mu_1 = b4[1], mu_ne = b4[2];
+  const double norm_est = b4[3];
+  st.b_sup = b_sup;
+  st.mu_1 = mu_1;
+  st.mu_ne = mu_ne;
+  st.norm_est = norm_est;
+  const double tol_abs = P.tol * norm_est;
+
+  std::vector<int32_t> degs(ne, P.deg_init);
+  std::vector<double> rz(ne, 0.0), rs(ne, 0.0);
+  std::vector<int> perm(ne);
+  double* rz_pin = c->host;
+  double* rs_pin = c->host + ne;
+  int64_t locked = 0;
+  int iter = 1;
+  double cc = (b_sup + mu_ne) / 2.0, ee = (b_sup - mu_ne) / 2.0;
+  bool mixed = P.precision == CHASE_MIXED_BF16X3;
+  double rmax_prev = 1e300;
+  st.switch_iter = mixed ? -1 : 0;
+
+  while (locked < nev && iter <= P.max_iter) {
+    const int64_t nact = ne - locked;
+    if (iter != 1) {
+      mu_1 = *std::min_element(rz.begin(), rz.end());
+      mu_ne = *std::max_element(rz.begin(), rz.end());
+      cc = (b_sup + mu_ne) / 2.0;
+      ee = (b_sup - mu_ne) / 2.0;
+      if (P.deg_opt) {
+        chase_degree_opt(rs.data() + locked, rz.data() + locked, nact, cc, ee, tol_abs, P.deg_max,
+                         P.deg_extra, degs.data() + locked);
+        std::vector<int> ord(nact);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+          const int32_t da = degs[locked + a], db = degs[locked + b];
+          if (da != db) return da < db;
+          return rz[locked + a] < rz[locked + b];
+        });
+        bool ident = true;
+        for (int64_t k = 0; k < nact; ++k) ident = ident && ord[k] == k;
+        if (!ident) {
+          std::vector<int32_t> d2(nact);
+          std::vector<double> z2(nact), s2(nact);
+          for (int64_t k = 0; k < nact; ++k) {
+            d2[k] = degs[locked + ord[k]];
+            z2[k] = rz[locked + ord[k]];
+            s2[k] = rs[locked + ord[k]];
+          }
+          std::copy(d2.begin(), d2.end(), degs.begin() + locked);
+          std::copy(z2.begin(), z2.end(), rz.begin() + locked);
+          std::copy(s2.begin(), s2.end(), rs.begin() + locked);
+          CK(cudaMemcpyAsync(c->perm_d, ord.data(), nact * sizeof(int), cudaMemcpyHostToDevice,
+                             c->stream));
+          CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->W, N));
+          CK(gather_cols(c->stream, N, nact, c->W, N, c->perm_d, C + locked * ldv, ldv));
+          CK(cudaStreamSynchronize(c->stream));  // ord is a stack buffer
+        }
+      }
+    }
+    double cond;
+    if (iter == 1) {
+      std::vector<double> lam(ne, mu_1);
+      cond = chase_cond_est(lam.data(), degs.data(), ne, locked, cc, ee);
+    } else {
+      cond = chase_cond_est(rz.data(), degs.data(), ne, locked, cc, ee);
+    }
+    const int prec = mixed ? CHASE_MIXED_BF16X3 : CHASE_FP64;
+    RC(filter_impl(c, A, lda, C + locked * ldv, ldv, nact, degs.data() + locked, cc, ee, mu_1,
+                   prec, &st.ms_filter));
+    int64_t mv = 0;
+    for (int64_t j = locked; j < ne; ++j) mv += degs[j];
+    st.matvecs += mv;
+    if (mixed) st.matvecs_mixed += mv;
+    int32_t variant = 0;
+    {
+      PhaseTimer tm(c, &st.ms_qr);
+      RC(qr_impl(c, C, ldv, ne, cond, &variant));
+      CK(copy_cols(c->stream, N, locked, c->V2, N, C, ldv));                       // C[:, :locked] = C2
+      CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
+    }
+    if (variant >= 1 && variant <= 4) st.qr_variant_count[variant]++;
+    {
+      PhaseTimer tm(c, &st.ms_rr);
+      RC(rr_impl(c, A, lda, c->V2 + locked * N, N, C + locked * ldv, ldv, nact, ritz + locked));
+      CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
+    }
+    {
+      PhaseTimer tm(c, &st.ms_resid);
+      RC(resid_impl(c, A, lda, C + locked * ldv, ldv, ritz + locked, nact, resid + locked));
+    }
+    CK(cudaMemcpyAsync(rz_pin, ritz + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(rs_pin, resid + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::copy(rz_pin, rz_pin + nact, rz.begin() + locked);
+    std::copy(rs_pin, rs_pin + nact, rs.begin() + locked);
+    int64_t nc = 0;
+    while (locked + nc < ne && rs[locked + nc] <= tol_abs) ++nc;
+    // precision switch (reading of the mixed-precision policy): leave the
+    // reduced-precision filter once the largest residual among the wanted active
+    // pairs reaches switch_tol, or stops falling by at least 3x per iteration.
+    if (mixed) {
+      double rmax = 0.0;
+      for (int64_t j = locked + nc; j < nev; ++j) rmax = std::max(rmax, rs[j] / norm_est);
+      if (rmax <= P.switch_tol || rmax > rmax_prev / 3.0) {
+        mixed = false;
+        st.switch_iter = iter;
+      }
+      rmax_prev = rmax;
+    }
+    locked += nc;
+    ++iter;
+  }
+  // Output: the first nev Ritz pairs in ascending order (Alg. 2 "Return").
+  const int64_t nsort = std::max<int64_t>(locked, nev);
+  std::vector<int> ord(nsort);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return rz[a] < rz[b]; });
+  bool ident = true;
+  for (int64_t k = 0; k < nev; ++k) ident = ident && ord[k] == k;
+  if (!ident) {
+    std::vector<double> z2(nev), s2(nev);
+    for (int64_t k = 0; k < nev; ++k) {
+      z2[k] = rz[ord[k]];
+      s2[k] = rs[ord[k]];
+    }
+    CK(cudaMemcpyAsync(c->perm_d, ord.data(), nev * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(copy_cols(c->stream, N, nsort, C, ldv, c->W, N));
+    CK(gather_cols(c->stream, N, nev, c->W, N, c->perm_d, C, ldv));
+    CK(cudaMemcpyAsync(ritz, z2.data(), nev * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(resid, s2.data(), nev * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaEventRecord(t_end, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, t_start, t_end);
+  cudaEventDestroy(t_start);
+  cudaEventDestroy(t_end);
+  st.ms_total = ms;
+  st.iters = iter - 1;
+  st.locked = (int32_t)locked;
+  st.filter_flops = 8.0 * (double)N * (double)N * (double)st.matvecs;
+  if (stats) *stats = st;
+  return locked >= nev ? CHASE_OK : CHASE_ERR_NOT_CONVERGED;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the kernel translation units and the host
+// driver. Complex128 values are double2 (x = real, y = imaginary), matrices are
+// column-major with explicit leading dimensions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/chase.h"
+
+namespace chase {
+
+// ----------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ double2 cscale(double s, double2 a) {
+  return make_double2(s * a.x, s * a.y);
+}
+__host__ __device__ __forceinline__ double2 conjz(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b with four fused multiply-adds
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------- GEMM (FP64)
+// Epilogue of the complex FP64 GEMM  P = A * B  (M x n, K inner).
+enum EpiMode { EPI_STORE = 0, EPI_FILTER = 1, EPI_RESID = 2 };
+struct Epilogue {
+  int mode;
+  double alpha, beta, gamma;  // filter: out = alpha (P - gamma X) + beta Y
+  const double2* X;           // filter/resid: the B operand read element-wise
+  int64_t ldx;
+  double2* Y;                 // store / filter destination
+  int64_t ldy;
+  const double* theta;        // resid: Ritz values per column
+  double* partial;            // resid: [row_tile + col * n_row_tiles] sums of |.|^2
+};
+
+// P = A (M x K) * B (K x n); A column-major (lda), B column-major (ldb).
+cudaError_t zgemm_nn(cudaStream_t s, int64_t M, int64_t n, int64_t K, const double2* A,
+                     int64_t lda, const double2* B, int64_t ldb, const Epilogue& ep);
+// Number of 64-row tiles the residual epilogue writes partials for.
+int64_t zgemm_row_tiles(int64_t M);
+// Fixed-order reduction of the residual partials: out[j] = sqrt(sum_t partial).
+cudaError_t resid_reduce(cudaStream_t s, const double* partial, int64_t ntiles, int64_t n,
+                         double* out);
+
+// Gram products G = X^H Y (m x n) over K rows, split-K with a deterministic
+// reduction. hermitian: X == Y, only upper tiles computed, G made exactly
+// Hermitian. make_hermitian (non-Hermitian input): G <- (G + G^H) / 2.
+size_t gram_workspace_elems(int64_t m, int64_t n);
+cudaError_t zgram(cudaStream_t s, int64_t K, int64_t m, int64_t n, const double2* X,
+                  int64_t ldx, const double2* Y, int64_t ldy, double2* G, int64_t ldg,
+                  bool hermitian, double2* ws, size_t ws_elems);
+cudaError_t hermitian_part(cudaStream_t s, int64_t n, double2* G, int64_t ldg);
+
+// Skinny product P = A * B for n <= 8 columns (Lanczos), split-K partials in ws.
+size_t skinny_workspace_elems(int64_t M, int64_t n);
+cudaError_t zgemm_skinny(cudaStream_t s, int64_t M, int64_t n, const double2* A, int64_t lda,
+                         const double2* B, int64_t ldb, double2* P, int64_t ldp, double2* ws);
+
+// -------------------------------------------------------- factorisations
+// Upper Cholesky G = U^H U in place (n x n, ldg); *info (device) = 0 or the
+// 1-based first failing pivot. dinv receives the inverses of the 64 x 64
+// diagonal blocks of U (ceil(n/64) blocks of 64*64, column-major).
+constexpr int kNB = 64;
+cudaError_t potrf_upper(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double2* dinv,
+                        int* info);
+// X <- X U^{-1} (X: m x n, ldx), U upper from potrf_upper with its dinv.
+cudaError_t trsm_right_upper(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx,
+                             const double2* U, int64_t ldu, const double2* dinv,
+                             const int* info);
+// G_ii += shift * trace(G) (device scalars only); used for the shifted pass.
+cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double factor,
+                            double* scratch);
+
+// ------------------------------------------------------------ eigensolver
+// Two-sided cyclic Jacobi with round-robin parallel ordering on the n x n
+// Hermitian G (destroyed). Eigenvalues ascending into w (device), eigenvectors
+// into Z (n x n, ldz). *sweeps_out (host) and the status.
+struct JacobiWork {
+  double2* Gw;       // n x n working copy (ld n)
+  double2* Zw;       // n x n unsorted eigenvectors (ld n)
+  double* params;    // 4 per pair
+  double* red;       // reduction scratch
+  double* host_red;  // pinned host scalars
+  int64_t nmax;
+};
+size_t jacobi_params_elems(int64_t n);
+int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
+                int64_t ldz, JacobiWork& wk, int* sweeps_out);
+// Batched small Jacobi (n <= 64) on `batch` column-major n x n matrices with
+// stride n*n; eigenvalues ascending (w: batch x n), eigenvectors Z; *status
+// (device) set to 1 when a sweep cap is hit.
+cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2* G, double* w,
+                                 double2* Z, int* status);
+
+// -------------------------------------------------------------- vector ops
+cudaError_t copy_cols(cudaStream_t s, int64_t m, int64_t n, const double2* src, int64_t lds,
+                      double2* dst, int64_t ldd);
+cudaError_t gather_cols(cudaStream_t s, int64_t m, int64_t n, const double2* src, int64_t lds,
+                        const int* perm, double2* dst, int64_t ldd);
+
+// Lanczos with nvec simultaneous runs (block HEMV + per-run BLAS-1); writes
+// bounds (b_sup, mu_1, mu_ne, norm_est) to the device array out4.
+struct LanczosWork {
+  double2* Q;        // 3 buffers of N x 8 (prev, cur, next/w)
+  double2* ws;       // skinny GEMM workspace
+  double* red;       // partial sums
+  double* ab;        // alpha/beta per run and step: [2][8][kmax]
+  double2* T;        // batch of k x k tridiagonal matrices as complex
+  double* theta;     // batch x k
+  double2* Z;        // batch x k x k
+  double* out4;      // b_sup, mu_1, mu_ne, norm_est
+  int* status;
+};
+cudaError_t lanczos_bounds(cudaStream_t s, int64_t N, const double2* A, int64_t lda,
+                           const double2* Q0, int64_t ldq, int nvec, int k, int64_t ne,
+                           LanczosWork& w);
+
+}  // namespace chase
