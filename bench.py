@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the single-GPU ChASE hot path.
+
+Workload (default ``--config C2``): complex Hermitian A with N = 20000,
+nev = 1000, nex = 300, geometric spectrum 1e-4 .. 1, A = H D H^H with 16
+Householder reflectors, FP64. One step is one pass of the whole hot path
+through the C ABI (``chase_solve`` with max_iter = 1): Lanczos bounds, then one
+ChASE iteration (filter of all 1300 vectors at the initial degree 20, CondEst,
+1D-CAQR, restore, Rayleigh-Ritz with Jacobi, residuals, locking and the degree
+update). This is the paper's own unit of measurement for its weak-scaling runs
+(one iteration at fixed nev/nex, Section 4.5).
+
+Printed: one JSON line. ``value`` = ChASE iterations per second over the whole
+job (N replicas for --gpus N; the solve does not shard, see the design notes).
+``--impl reference`` times the CPU FP64 oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution at resid≤1e-10, mixed vs FP64; filter TFLOP/s vs peak"
+# FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="C2")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(p, deg):
+    return (f"{p.spectrum} spectrum, N={p.N}, nev={p.nev}, nex={p.nex}, {p.reflectors} Householder "
+            f"reflectors; step = Lanczos bounds + one ChASE iteration (filter degree {deg} on "
+            f"{p.ne} vectors, CondEst, CAQR, Rayleigh-Ritz, residuals, locking)")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(A, V0, p, deg, ncols=128):
+    """Times the oracle on a bounded sample of one ChASE iteration at full N and
+    extrapolates to the whole iteration: the filter and residual HEMMs on
+    ``ncols`` of the vectors (scaled by columns x degrees), the full-size CAQR
+    and the full-size small eigenproblem. Returns (seconds per iteration,
+    sample description, measured seconds)."""
+    from oracle import chase_oracle as O
+
+    ne = p.ne
+    lam = p.eigenvalues()
+    b_sup = lam[-1] * 1.01
+    c, e, mu1 = (b_sup + lam[ne - 1]) / 2, (b_sup - lam[ne - 1]) / 2, lam[0]
+    Vs = np.asfortranarray(V0[:, :ncols])
+    ds = 4
+    t0 = time.perf_counter()
+    Y = O.chebyshev_filter(A, Vs, np.full(ncols, ds), c, e, mu1)
+    t1 = time.perf_counter()
+    O.residuals(A, Y, np.linspace(lam[0], lam[ne], ncols))
+    t2 = time.perf_counter()
+    O.caqr(V0, 1e4)
+    t3 = time.perf_counter()
+    G = V0[:ne, :ne] + V0[:ne, :ne].conj().T
+    np.linalg.eigh(G)
+    t4 = time.perf_counter()
+    per_colmv = (t1 - t0) / (ncols * ds)
+    per_col_resid = (t2 - t1) / ncols
+    t_iter = per_colmv * ne * deg + 2 * per_col_resid * ne + (t3 - t2) + (t4 - t3)
+    desc = (f"oracle at full N={p.N}: filter degree {ds} on {ncols} of {ne} vectors, residuals of "
+            f"{ncols} vectors, CAQR (CholeskyQR2) of the full {p.N}x{ne} block, eigh of a "
+            f"{ne}x{ne} matrix; HEMM parts scaled to {ne} vectors x degree {deg} (+2 HEMMs for RR "
+            f"and residuals)")
+    return t_iter, desc, t4 - t0
+
+
+def build_matrix_host(p):
+    import torch
+
+    if torch.cuda.is_available():
+        Ad = p.matrix_torch("cuda")
+        A = np.asfortranarray(Ad.cpu().numpy())
+        del Ad
+        torch.cuda.empty_cache()
+        return A
+    return p.matrix()
+
+
+def run_reference(args):
+    from synth import config_problem
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = config_problem(args.config)
+    A = build_matrix_host(p)
+    V0 = p.start_block()
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample(A, V0, p, 20)
+    times, desc, meas = [], "", 0.0
+    for _ in range(args.steps):
+        t, desc, m = oracle_sample(A, V0, p, 20)
+        times.append(t)
+        meas += m
+    t_iter = sum(times) / len(times)
+    value = 1.0 / t_iter
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ChASE iterations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * t_iter, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: " + workload_desc(p, 20), "N": p.N,
+                   "nev": p.nev, "nex": p.nex, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "ChASE iterations/s", "cores": cores,
+                         "kind": "oracle", "sample": desc + f" (measured {meas:.1f} s)"},
+        "e2e": {"value": value, "unit": "ChASE iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU
+def run_gpu(args):
+    import torch
+
+    import paper_2309_15595_gb300 as lib
+    from synth import config_problem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    p = config_problem(args.config)
+    N, ne = p.N, p.ne
+    prec = lib.CHASE_FP64 if args.precision == "fp64" else lib.CHASE_MIXED_BF16X3
+    params = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec)
+    deg = int(params.deg_init)
+    Ad = p.matrix_torch(dev)
+    V0d = lib.colmajor(torch.from_numpy(p.start_block()).to(dev))
+    Q0d = lib.colmajor(torch.from_numpy(p.lanczos_start()).to(dev))
+    V = lib.colmajor(torch.empty_like(V0d))
+    ritz = torch.zeros(ne, dtype=torch.float64, device=dev)
+    resid = torch.zeros_like(ritz)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lib.Context(params, stream)
+
+    def step():
+        V.copy_(V0d)
+        return ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # dominant kernel: the filter GEMM (deg launches per iteration at iteration 1,
+    # all ne vectors active); per-launch time from the library's CUDA events on
+    # the launching stream over the timed steps
+    ms_filter = sum(s["ms_filter"] for s in stats) / len(stats)
+    launch_ms = ms_filter / deg
+    flops_launch = 8.0 * N * N * ne
+    achieved = flops_launch / (launch_ms / 1000.0) / 1e12
+    phases = {k: sum(s[k] for s in stats) / len(stats) for k in
+              ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid", "ms_total")}
+    launches = int(sum(s["kernel_launches"] for s in stats))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "ChASE iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == lib.CHASE_FP64 else "bf16x3+f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: " + workload_desc(p, deg), "N": N, "nev": p.nev,
+                   "nex": p.nex, "deg": deg, "precision": args.precision,
+                   "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * N * N / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "zgemm_kernel<EPI_FILTER> (filter HEMM, Eq. 1)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "launches_per_step": deg, "flops_per_launch": flops_launch,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz"},
+        "filter_tflops": 8.0 * N * N * stats[-1]["matvecs"] / (ms_filter / 1000.0) / 1e12,
+        "phase_ms": phases,
+        "gpu_launches": launches,
+        "qr_variant": stats[-1]["qr_variant_count"],
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        # same step with HOST buffers: H2D of A, start block and Lanczos vectors,
+        # D2H of the Ritz values, residuals and vectors, inside the timed region
+        A_h = torch.empty_strided((N, N), (1, N), dtype=torch.complex128, pin_memory=True)
+        A_h.copy_(Ad)
+        V0_h = torch.empty_strided((N, ne), (1, N), dtype=torch.complex128, pin_memory=True)
+        V0_h.copy_(V0d)
+        Q0_h = torch.empty_strided(tuple(Q0d.shape), (1, N), dtype=torch.complex128,
+                                   pin_memory=True)
+        Q0_h.copy_(Q0d)
+        V_out = torch.empty_strided((N, ne), (1, N), dtype=torch.complex128, pin_memory=True)
+        rz_out = torch.empty(ne, dtype=torch.float64, pin_memory=True)
+        rs_out = torch.empty(ne, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+
+        def step_e2e():
+            Ad.copy_(A_h, non_blocking=True)
+            V.copy_(V0_h, non_blocking=True)
+            Q0d.copy_(Q0_h, non_blocking=True)
+            ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+            V_out.copy_(V, non_blocking=True)
+            rz_out.copy_(ritz, non_blocking=True)
+            rs_out.copy_(resid, non_blocking=True)
+
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        line["e2e"] = {"value": world * args.steps / (ems / 1000.0), "unit": "ChASE iterations/s",
+                       "h2d_bytes_per_step": 16 * (N * N + N * ne + N * Q0d.shape[1]),
+                       "d2h_bytes_per_step": 16 * N * ne + 16 * ne}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            A_np = A_h.numpy()
+            t_iter, desc, meas = oracle_sample(A_np, V0_h.numpy(), p, deg)
+            line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "ChASE iterations/s",
+                                    "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": desc + f" (measured {meas:.1f} s)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,7 @@ typedef struct chase_stats {
   double filter_flops;    /* 8 N^2 per MatVec */
   int32_t qr_variant_count[5];  /* index = CHASE_QR_* */
   int32_t switch_iter;    /* iteration at which the filter became FP64 (0: never mixed) */
+  int64_t kernel_launches;  /* kernels this library launched during the solve */
 } chase_stats;
 
 /* Fills *p with the defaults above for the given sizes. Host only. */

@@ -53,6 +53,7 @@ class ChaseStats(ctypes.Structure):
         ("filter_flops", ctypes.c_double),
         ("qr_variant_count", ctypes.c_int32 * 5),
         ("switch_iter", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

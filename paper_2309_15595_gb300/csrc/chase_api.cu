@@ -5,6 +5,7 @@
 // arrays of nev + nex doubles; every vector and matrix operation runs in the
 // kernels of this library on the context's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,12 @@
 #include "mixed.cuh"
 
 using namespace chase;
+
+namespace chase {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace chase
 
 struct chase_ctx {
   chase_params p;
@@ -470,6 +477,7 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   CK(cudaEventCreate(&t_start));
   CK(cudaEventCreate(&t_end));
   CK(cudaEventRecord(t_start, c->stream));
+  const long long launches0 = launch_count();
 
   double b4[4];
   {
@@ -622,6 +630,7 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   st.iters = iter - 1;
   st.locked = (int32_t)locked;
   st.filter_flops = 8.0 * (double)N * (double)N * (double)st.matvecs;
+  st.kernel_launches = launch_count() - launches0;
   if (stats) *stats = st;
   return locked >= nev ? CHASE_OK : CHASE_ERR_NOT_CONVERGED;
 }

@@ -38,6 +38,10 @@ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Process-wide count of kernel launches issued by this library.
+void count_launch();
+long long launch_count();
+
 // ------------------------------------------------------------- GEMM (FP64)
 // Epilogue of the complex FP64 GEMM  P = A * B  (M x n, K inner).
 enum EpiMode { EPI_STORE = 0, EPI_FILTER = 1, EPI_RESID = 2 };

@@ -283,13 +283,13 @@ cudaError_t potrf_upper(cudaStream_t s, int64_t n, double2* G, int64_t ldg, doub
   const size_t sm2 = 2 * NB * NB * sizeof(double2);
   for (int64_t k0 = 0, b = 0; k0 < n; k0 += NB, ++b) {
     const int kb = (int)std::min<int64_t>(NB, n - k0);
-    potf2_kernel<<<1, FT, sm2, s>>>(G, ldg, k0, kb, dinv + b * NB * NB, info);
+    potf2_kernel<<<1, FT, sm2, s>>>(G, ldg, k0, kb, dinv + b * NB * NB, info); count_launch();
     const int64_t rest = n - k0 - kb;
     if (rest > 0) {
       panel_kernel<<<(unsigned)cdiv(rest, NB), FT, sm2, s>>>(n, G, ldg, k0, kb, dinv + b * NB * NB,
-                                                             info);
+                                                             info); count_launch();
       const unsigned tt = (unsigned)cdiv(rest, NB);
-      trailing_kernel<<<dim3(tt, tt, 1), FT, 0, s>>>(n, G, ldg, k0, kb, info);
+      trailing_kernel<<<dim3(tt, tt, 1), FT, 0, s>>>(n, G, ldg, k0, kb, info); count_launch();
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -302,13 +302,13 @@ cudaError_t trsm_right_upper(cudaStream_t s, int64_t m, int64_t n, double2* X, i
   set_attrs();
   if (m <= 0 || n <= 0) return cudaSuccess;
   const size_t smem = (NB * RP + NB * NB + TK * RP + TK * NB) * sizeof(double2);
-  trsm_kernel<<<(unsigned)cdiv(m, RP), FT, smem, s>>>(m, n, X, ldx, U, ldu, dinv, info);
+  trsm_kernel<<<(unsigned)cdiv(m, RP), FT, smem, s>>>(m, n, X, ldx, U, ldu, dinv, info); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double factor,
                             double* scratch) {
-  trace_shift_kernel<<<1, 256, 0, s>>>(n, G, ldg, factor, scratch);
+  trace_shift_kernel<<<1, 256, 0, s>>>(n, G, ldg, factor, scratch); count_launch();
   return cudaGetLastError();
 }
 

@@ -310,7 +310,7 @@ cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2
                          (int)smem);
     g_small_attr = true;
   }
-  jacobi_small_kernel<<<batch, SJ_T, smem, s>>>(n, G, w, Z, status);
+  jacobi_small_kernel<<<batch, SJ_T, smem, s>>>(n, G, w, Z, status); count_launch();
   return cudaGetLastError();
 }
 
@@ -340,14 +340,14 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   }
   const int m = (int)(n + (n & 1));
   const int npairs = m / 2;
-  init_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, G, ldg, wk.Gw, wk.Zw);
+  init_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, G, ldg, wk.Gw, wk.Zw); count_launch();
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   double off_prev = 1e300;
   bool conv = false;
   int sweep = 0;
   for (; sweep <= kMaxSweeps; ++sweep) {
-    offnorm_partial_kernel<<<RED_BLOCKS, 256, 0, s>>>(n, wk.Gw, wk.red);
-    offnorm_final_kernel<<<1, 32, 0, s>>>(wk.red, wk.red + 2 * RED_BLOCKS);
+    offnorm_partial_kernel<<<RED_BLOCKS, 256, 0, s>>>(n, wk.Gw, wk.red); count_launch();
+    offnorm_final_kernel<<<1, 32, 0, s>>>(wk.red, wk.red + 2 * RED_BLOCKS); count_launch();
     e = cudaMemcpyAsync(wk.host_red, wk.red + 2 * RED_BLOCKS, 2 * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CHASE_ERR_CUDA;
@@ -359,15 +359,15 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     off_prev = off;
     if (sweep == kMaxSweeps) break;
     for (int round = 0; round < m - 1; ++round) {
-      col_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.Zw, wk.params);
-      row_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.params);
+      col_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.Zw, wk.params); count_launch();
+      row_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.params); count_launch();
     }
     if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   }
   int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
-  rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, w, rank);
+  rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, w, rank); count_launch();
   permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, wk.Zw, rank,
-                                                                                    Z, ldz);
+                                                                                    Z, ldz); count_launch();
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   if (sweeps_out) *sweeps_out = sweep;
   return conv ? CHASE_OK : CHASE_ERR_HEEV_NOCONV;

@@ -163,7 +163,7 @@ cudaError_t copy_cols(cudaStream_t s, int64_t m, int64_t n, const double2* src, 
                       double2* dst, int64_t ldd) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   copy_cols_kernel<<<dim3((unsigned)cdiv(m, 256), (unsigned)n, 1), 256, 0, s>>>(m, src, lds, dst,
-                                                                                 ldd);
+                                                                                 ldd); count_launch();
   return cudaGetLastError();
 }
 
@@ -171,7 +171,7 @@ cudaError_t gather_cols(cudaStream_t s, int64_t m, int64_t n, const double2* src
                         const int* perm, double2* dst, int64_t ldd) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   gather_cols_kernel<<<dim3((unsigned)cdiv(m, 256), (unsigned)n, 1), 256, 0, s>>>(m, src, lds,
-                                                                                   perm, dst, ldd);
+                                                                                   perm, dst, ldd); count_launch();
   return cudaGetLastError();
 }
 
@@ -188,34 +188,34 @@ cudaError_t lanczos_bounds(cudaStream_t s, int64_t N, const double2* A, int64_t 
   const dim3 ge((unsigned)cdiv(N, 256), (unsigned)nvec, 1);
   // q = q0 / ||q0||
   lz_partial_kernel<<<gp, VT, 0, s>>>(0, N, nvec, Q0, ldq, nullptr, nullptr, nullptr, w.ab, 0,
-                                      kmax, w.red);
-  lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, norms, kmax, 0, 1);
-  lz_scale_kernel<<<ge, 256, 0, s>>>(N, nvec, Q0, ldq, Q, norms, kmax, 0);
-  lz_zero_kernel<<<(unsigned)cdiv(N * 8, 256), 256, 0, s>>>(N * 8, Qp);
+                                      kmax, w.red); count_launch();
+  lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, norms, kmax, 0, 1); count_launch();
+  lz_scale_kernel<<<ge, 256, 0, s>>>(N, nvec, Q0, ldq, Q, norms, kmax, 0); count_launch();
+  lz_zero_kernel<<<(unsigned)cdiv(N * 8, 256), 256, 0, s>>>(N * 8, Qp); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int j = 0; j < k; ++j) {
     e = zgemm_skinny(s, N, nvec, A, lda, Q, N, W, N, w.ws);  // W = A q
     if (e != cudaSuccess) return e;
     // W -= beta_{j-1} q_prev ; alpha_j = Re(q^H W)
-    lz_partial_kernel<<<gp, VT, 0, s>>>(1, N, nvec, nullptr, 0, Q, Qp, W, w.ab, j, kmax, w.red);
-    lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, w.ab, kmax, j, 0);
+    lz_partial_kernel<<<gp, VT, 0, s>>>(1, N, nvec, nullptr, 0, Q, Qp, W, w.ab, j, kmax, w.red); count_launch();
+    lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, w.ab, kmax, j, 0); count_launch();
     // W -= alpha_j q ; beta_j = ||W||
-    lz_partial_kernel<<<gp, VT, 0, s>>>(2, N, nvec, nullptr, 0, Q, Qp, W, w.ab, j, kmax, w.red);
-    lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, w.ab + 8 * kmax, kmax, j, 1);
+    lz_partial_kernel<<<gp, VT, 0, s>>>(2, N, nvec, nullptr, 0, Q, Qp, W, w.ab, j, kmax, w.red); count_launch();
+    lz_final_kernel<<<1, 32, 0, s>>>(nvec, w.red, w.ab + 8 * kmax, kmax, j, 1); count_launch();
     if (j + 1 < k) {
       // q_prev <- q ; q <- W / beta_j  (the old q_prev buffer receives the new q)
-      lz_scale_kernel<<<ge, 256, 0, s>>>(N, nvec, W, N, Qp, w.ab + 8 * kmax, kmax, j);
+      lz_scale_kernel<<<ge, 256, 0, s>>>(N, nvec, W, N, Qp, w.ab + 8 * kmax, kmax, j); count_launch();
       std::swap(Qp, Q);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  lz_build_t_kernel<<<nvec, 256, 0, s>>>(nvec, k, kmax, w.ab, w.T);
+  lz_build_t_kernel<<<nvec, 256, 0, s>>>(nvec, k, kmax, w.ab, w.T); count_launch();
   e = jacobi_small_batched(s, k, nvec, w.T, w.theta, w.Z, w.status);
   if (e != cudaSuccess) return e;
   lz_bounds_kernel<<<1, 256, 0, s>>>(nvec, k, kmax, w.ab, w.theta, w.Z, (double)ne / (double)N,
-                                     w.out4);
+                                     w.out4); count_launch();
   return cudaGetLastError();
 }
 

@@ -297,13 +297,13 @@ cudaError_t zgemm_nn(cudaStream_t s, int64_t M, int64_t n, int64_t K, const doub
   dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(n, BN), 1);
   switch (ep.mode) {
     case EPI_STORE:
-      zgemm_kernel<false, EPI_STORE><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false);
+      zgemm_kernel<false, EPI_STORE><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false); count_launch();
       break;
     case EPI_FILTER:
-      zgemm_kernel<false, EPI_FILTER><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false);
+      zgemm_kernel<false, EPI_FILTER><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false); count_launch();
       break;
     default:
-      zgemm_kernel<false, EPI_RESID><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false);
+      zgemm_kernel<false, EPI_RESID><<<grid, NT, 0, s>>>(M, n, K, A, lda, B, ldb, ep, K, 0, false); count_launch();
       break;
   }
   return cudaGetLastError();
@@ -312,7 +312,7 @@ cudaError_t zgemm_nn(cudaStream_t s, int64_t M, int64_t n, int64_t K, const doub
 cudaError_t resid_reduce(cudaStream_t s, const double* partial, int64_t ntiles, int64_t n,
                          double* out) {
   if (n <= 0) return cudaSuccess;
-  resid_reduce_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(partial, ntiles, n, out);
+  resid_reduce_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(partial, ntiles, n, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -336,18 +336,18 @@ cudaError_t zgram(cudaStream_t s, int64_t K, int64_t m, int64_t n, const double2
   ep.ldy = m;
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
   zgemm_kernel<true, EPI_STORE><<<grid, NT, 0, s>>>(m, n, K, X, ldx, Y, ldy, ep, kchunk,
-                                                    m * n, hermitian);
+                                                    m * n, hermitian); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 g2((unsigned)cdiv(m, 128), (unsigned)n, 1);
-  gram_reduce_kernel<<<g2, 128, 0, s>>>(m, n, (int)splits, ws, G, ldg, hermitian);
+  gram_reduce_kernel<<<g2, 128, 0, s>>>(m, n, (int)splits, ws, G, ldg, hermitian); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t hermitian_part(cudaStream_t s, int64_t n, double2* G, int64_t ldg) {
   if (n <= 0) return cudaSuccess;
   dim3 g((unsigned)cdiv(n, 128), (unsigned)n, 1);
-  hermitian_part_kernel<<<g, 128, 0, s>>>(n, G, ldg);
+  hermitian_part_kernel<<<g, 128, 0, s>>>(n, G, ldg); count_launch();
   return cudaGetLastError();
 }
 
@@ -367,17 +367,17 @@ cudaError_t zgemm_skinny(cudaStream_t s, int64_t M, int64_t n, const double2* A,
   dim3 grid((unsigned)rt, (unsigned)splits, 1);
   const unsigned rb = (unsigned)cdiv(M, 128);
   if (n <= 1) {
-    skinny_kernel<1><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk);
-    skinny_reduce_kernel<1><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp);
+    skinny_kernel<1><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk); count_launch();
+    skinny_reduce_kernel<1><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp); count_launch();
   } else if (n <= 2) {
-    skinny_kernel<2><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk);
-    skinny_reduce_kernel<2><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp);
+    skinny_kernel<2><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk); count_launch();
+    skinny_reduce_kernel<2><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp); count_launch();
   } else if (n <= 4) {
-    skinny_kernel<4><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk);
-    skinny_reduce_kernel<4><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp);
+    skinny_kernel<4><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk); count_launch();
+    skinny_reduce_kernel<4><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp); count_launch();
   } else {
-    skinny_kernel<8><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk);
-    skinny_reduce_kernel<8><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp);
+    skinny_kernel<8><<<grid, SK_ROWS, 0, s>>>(M, (int)n, A, lda, B, ldb, ws, kchunk); count_launch();
+    skinny_reduce_kernel<8><<<rb, 128, 0, s>>>(M, (int)n, (int)splits, ws, P, ldp); count_launch();
   }
   return cudaGetLastError();
 }
