@@ -119,6 +119,7 @@ def oracle_sample(A, V0, p, deg, ncols=128):
     lam = p.eigenvalues()
     b_sup = lam[-1] * 1.01
     c, e, mu1 = (b_sup + lam[ne - 1]) / 2, (b_sup - lam[ne - 1]) / 2, lam[0]
+    ncols = min(ncols, ne)
     Vs = np.asfortranarray(V0[:, :ncols])
     ds = 4
     t0 = time.perf_counter()

@@ -1,17 +1,488 @@
-// Placeholder until the tensor-core filter lands: the mixed mode reports
-// CHASE_ERR_INVALID_ARG.
+// Reduced-precision Chebyshev filter on the 5th-generation tensor cores.
+//
+// Complex product as one real GEMM (planar, no wasted flops):
+//   [Wr | Wi] = [Ar | Ai] * [[Yr, Yi], [-Yi, Yr]]        (M = N, K = 2N, cols = 2n)
+// Every real operand x is split into two BF16 planes, hi = bf16(x),
+// lo = bf16(x - hi), and the product uses three MMAs per K block,
+// hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory (split-BF16 x3).
+// The recurrence state stays FP64: the epilogue reads the FP32 tile from TMEM,
+// forms Y_new = alpha (W - c Y_cur) + beta Y_prev in FP64 (Eq. 1), stores it over
+// Y_prev and also writes the BF16 hi/lo planes of Y_new in the K-major layout
+// the next step's MMA reads, so no separate conversion pass runs per degree.
+//
+// Kernel structure (one 128 x 256 output tile per CTA, 6 warps):
+//   warp 0   TMA producer: A_hi, A_lo (128 x 64) and B_hi, B_lo (256 x 64) per
+//            K block into a 2-stage shared-memory ring (128B swizzle)
+//   warp 1   TMEM allocator and single-thread MMA issuer (tcgen05.mma, M=128,
+//            N=256, K=16, kind::f16 with BF16 inputs)
+//   warps 2-5 epilogue: tcgen05.ld of their 32-lane TMEM quarter
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
+// records an error code and winds down instead of spinning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+
 #include "mixed.cuh"
 
 namespace chase {
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 64, STAGES = 2;
+constexpr int A_TILE = TM * TK * 2;                 // 16 KB
+constexpr int B_TILE = TN * TK * 2;                 // 32 KB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;  // 96 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+struct Params {
+  int64_t N, Np, j0, ncols;     // rows, padded K half, first active column, end column
+  const double2* Ycur;
+  int64_t ldc;
+  double2* Yprev;
+  int64_t ldp;
+  double alpha, beta, gamma;
+  __nv_bfloat16* Bn_hi;         // next-step operand planes (rows = B^T rows, ld = 2 Np)
+  __nv_bfloat16* Bn_lo;
+  int write_next;
+  int* err;
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and records `code`) after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// UMMA shared-memory descriptor, K-major operand with the 128-byte swizzle:
+// 8-row x 128-byte atoms, SBO = 1024 B between atoms, version 1 (sm_100+).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M x N.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+}
+
+// B^T row of complex column j: tile j/128 holds 256 rows, real parts first.
+__device__ __forceinline__ int64_t brow_re(int64_t j) { return (j >> 7) * 256 + (j & 127); }
+
+// ---------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mixed_filter_kernel(const __grid_constant__ CUtensorMap tmAh,
+                        const __grid_constant__ CUtensorMap tmAl,
+                        const __grid_constant__ CUtensorMap tmBh,
+                        const __grid_constant__ CUtensorMap tmBl, Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte alignment of the shared-window address (128B-swizzle atoms)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TM;
+  const int64_t tile = (P.j0 >> 7) + blockIdx.y;  // absolute 128-column tile
+  const int nkb = (int)((2 * P.Np) / TK);
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, P.err, 1)) {
+        s_abort = 1;
+        break;
+      }
+      if (*(volatile int*)&s_abort) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(full, STAGE_BYTES);
+      const int kx = kb * TK;
+      tma_load_2d(smem_u32(st), &tmAh, kx, (int)m0, full);
+      tma_load_2d(smem_u32(st + A_TILE), &tmAl, kx, (int)m0, full);
+      tma_load_2d(smem_u32(st + 2 * A_TILE), &tmBh, kx, (int)(tile * TN), full);
+      tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), &tmBl, kx, (int)(tile * TN), full);
+      ++issued;
+    }
+    // drain: every issued stage must land before the CTA may exit
+    for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+      mbar_wait(smem_u32(&bars[kb % STAGES]), (uint32_t)(kb / STAGES) & 1u, P.err, 2);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------- MMA issuer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bars[s]), ph, P.err, 3) || *(volatile int*)&s_abort) {
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = bh + B_TILE;
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk) {
+        const uint32_t off = kk * 32;  // 16 BF16 along K
+        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+        umma_bf16(tmem, sdesc_sw128(ah + off), sdesc_sw128(bh + off), acc0);
+        umma_bf16(tmem, sdesc_sw128(ah + off), sdesc_sw128(bl + off), 1u);
+        umma_bf16(tmem, sdesc_sw128(al + off), sdesc_sw128(bh + off), 1u);
+      }
+      umma_commit(smem_u32(&bars[STAGES + s]));  // stage free once these MMAs finish
+    }
+    umma_commit(smem_u32(&bars[2 * STAGES]));    // accumulator ready (or aborted)
+  } else if (warp >= 2) {
+    // ------------------------------------------------------- epilogue
+    const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0u, P.err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int64_t row = m0 + q * 32 + lane;
+    // warp-uniform decision: tcgen05.ld is a whole-warp instruction
+    const bool go = __all_sync(0xffffffffu, ok && !*(volatile int*)&s_abort);
+    if (go) {
+      for (int jc = 0; jc < 4; ++jc) {
+        float re[32], im[32];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16);
+        tmem_ld32(ta + jc * 32, re);
+        tmem_ld32(ta + 128 + jc * 32, im);
+        if (row >= P.N) continue;
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+          const int64_t col = tile * 128 + jc * 32 + jj;
+          if (col < P.j0 || col >= P.ncols) continue;
+          const double2 yc = P.Ycur[row + col * P.ldc];
+          double2* yp = P.Yprev + row + col * P.ldp;
+          double vr = P.alpha * ((double)re[jj] - P.gamma * yc.x);
+          double vi = P.alpha * ((double)im[jj] - P.gamma * yc.y);
+          if (P.beta != 0.0) {
+            const double2 y0 = *yp;
+            vr = fma(P.beta, y0.x, vr);
+            vi = fma(P.beta, y0.y, vi);
+          }
+          *yp = make_double2(vr, vi);
+          if (P.write_next) {
+            __nv_bfloat16 rh, rl, ih, il, nh, nl;
+            split2(vr, rh, rl);
+            split2(vi, ih, il);
+            split2(-vi, nh, nl);
+            const int64_t br = brow_re(col), bi = br + 128, ld = 2 * P.Np;
+            P.Bn_hi[br * ld + row] = rh;
+            P.Bn_lo[br * ld + row] = rl;
+            P.Bn_hi[br * ld + P.Np + row] = nh;
+            P.Bn_lo[br * ld + P.Np + row] = nl;
+            P.Bn_hi[bi * ld + row] = ih;
+            P.Bn_lo[bi * ld + row] = il;
+            P.Bn_hi[bi * ld + P.Np + row] = rh;
+            P.Bn_lo[bi * ld + P.Np + row] = rl;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------- conversions
+// A (column-major complex) -> row-major planes [Ar | Ai], K half padded to Np.
+__global__ void split_a_kernel(int64_t N, int64_t Np, const double2* __restrict__ A, int64_t lda,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  __shared__ double2 tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + tx, k = k0 + r;
+    tile[r][tx] = (i < N && k < N) ? A[i + k * lda] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int64_t ld = 2 * Np;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, k = k0 + tx;
+    if (i < N && k < N) {
+      const double2 a = tile[tx][r];
+      __nv_bfloat16 h, l;
+      split2(a.x, h, l);
+      hi[i * ld + k] = h;
+      lo[i * ld + k] = l;
+      split2(a.y, h, l);
+      hi[i * ld + Np + k] = h;
+      lo[i * ld + Np + k] = l;
+    }
+  }
+}
+
+// Columns j0..ncols of Y (column-major complex) -> B^T planes (K-major rows).
+__global__ void split_y_kernel(int64_t N, int64_t Np, int64_t j0, const double2* __restrict__ Y,
+                               int64_t ldy, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = j0 + blockIdx.y;
+  if (k >= N) return;
+  const double2 y = Y[k + j * ldy];
+  __nv_bfloat16 rh, rl, ih, il, nh, nl;
+  split2(y.x, rh, rl);
+  split2(y.y, ih, il);
+  split2(-y.y, nh, nl);
+  const int64_t br = brow_re(j), bi = br + 128, ld = 2 * Np;
+  hi[br * ld + k] = rh;
+  lo[br * ld + k] = rl;
+  hi[br * ld + Np + k] = nh;
+  lo[br * ld + Np + k] = nl;
+  hi[bi * ld + k] = ih;
+  lo[bi * ld + k] = il;
+  hi[bi * ld + Np + k] = rh;
+  lo[bi * ld + Np + k] = rl;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encoder() {
+  if (g_encode) return true;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+// rows x (2 Np) BF16, row-major; box = 64 (K) x box_rows.
+bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows) {
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * Np), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * Np * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+struct Maps {
+  CUtensorMap ah, al, bh[2], bl[2];
+};
+
+}  // namespace
+
+// Layout of MixedWork: Ahi/Alo = N x 2Np planes; Yhi/Ylo = two B^T plane pairs
+// (ping-pong), each brows x 2Np with brows = 256 * ceil(ne / 128); maps after.
 cudaError_t mixed_alloc(MixedWork& w, int64_t N, int64_t ne) {
   w.N = N;
   w.ne = ne;
-  return cudaErrorNotSupported;
+  const int64_t Np = cdiv(N, TK) * TK;
+  const int64_t brows = cdiv(ne, 128) * 256;
+  const size_t a_bytes = (size_t)N * 2 * Np * sizeof(__nv_bfloat16);
+  const size_t b_bytes = (size_t)brows * 2 * Np * sizeof(__nv_bfloat16);
+  if (!get_encoder()) return cudaErrorNotSupported;
+  cudaError_t e;
+  if ((e = cudaMalloc(&w.Ahi, a_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.Alo, a_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.Yhi, 2 * b_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.Ylo, 2 * b_bytes)) != cudaSuccess) return e;
+  // zero padding (K columns >= N of each half are never written afterwards)
+  if ((e = cudaMemset(w.Ahi, 0, a_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Alo, 0, a_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Yhi, 0, 2 * b_bytes)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Ylo, 0, 2 * b_bytes)) != cudaSuccess) return e;
+  Maps* maps = nullptr;
+  if ((e = cudaMallocHost(&maps, sizeof(Maps))) != cudaSuccess) return e;
+  w.maps = maps;
+  bool ok = make_map(&maps->ah, w.Ahi, N, Np, TM) && make_map(&maps->al, w.Alo, N, Np, TM);
+  for (int b = 0; b < 2; ++b) {
+    char* yh = static_cast<char*>(w.Yhi) + b * b_bytes;
+    char* yl = static_cast<char*>(w.Ylo) + b * b_bytes;
+    ok = ok && make_map(&maps->bh[b], yh, brows, Np, TN) && make_map(&maps->bl[b], yl, brows, Np, TN);
+  }
+  if (!ok) return cudaErrorInvalidValue;
+  if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.err, 0, sizeof(int))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mixed_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              SMEM_BYTES);
 }
-void mixed_free(MixedWork& w) { (void)w; }
-int mixed_filter(cudaStream_t, int64_t, const double2*, int64_t, double2*, int64_t, int64_t,
-                 const int32_t*, double, const double*, const double*, double2*, int64_t,
-                 MixedWork&) {
-  return CHASE_ERR_INVALID_ARG;
+
+void mixed_free(MixedWork& w) {
+  if (w.Ahi) cudaFree(w.Ahi);
+  if (w.Alo) cudaFree(w.Alo);
+  if (w.Yhi) cudaFree(w.Yhi);
+  if (w.Ylo) cudaFree(w.Ylo);
+  if (w.err) cudaFree(w.err);
+  if (w.maps) cudaFreeHost(w.maps);
+  w = MixedWork{};
 }
+
+int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, double2* V,
+                 int64_t ldv, int64_t ncols, const int32_t* degs, double c, const double* al,
+                 const double* be, double2* W, int64_t ldw, MixedWork& w) {
+  if (ncols == 0) return CHASE_OK;
+  if (!w.maps || N != w.N || ncols > w.ne) return CHASE_ERR_INVALID_ARG;
+  const Maps* maps = static_cast<const Maps*>(w.maps);
+  const int64_t Np = cdiv(N, TK) * TK;
+  const int64_t brows = cdiv(w.ne, 128) * 256;
+  const size_t b_elems = (size_t)brows * 2 * Np;
+  __nv_bfloat16* Yh = static_cast<__nv_bfloat16*>(w.Yhi);
+  __nv_bfloat16* Yl = static_cast<__nv_bfloat16*>(w.Ylo);
+  // planes of A, then of Y_0 = V into operand buffer 0
+  split_a_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(N, 32), 1), dim3(32, 8, 1), 0, s>>>(
+      N, Np, A, lda, static_cast<__nv_bfloat16*>(w.Ahi), static_cast<__nv_bfloat16*>(w.Alo));
+  count_launch();
+  split_y_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, Np, 0, V, ldv,
+                                                                                   Yh, Yl);
+  count_launch();
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_ERR_CUDA;
+  double2* buf[2] = {V, W};
+  const int64_t ld[2] = {ldv, ldw};
+  const int dmax = degs[ncols - 1];
+  for (int i = 1; i <= dmax; ++i) {
+    const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
+    const int src = (i - 1) & 1, dst = i & 1;   // FP64 state buffers
+    const int bin = (i - 1) & 1, bout = i & 1;  // operand plane buffers
+    Params P;
+    P.N = N;
+    P.Np = Np;
+    P.j0 = j0;
+    P.ncols = ncols;
+    P.Ycur = buf[src];
+    P.ldc = ld[src];
+    P.Yprev = buf[dst];
+    P.ldp = ld[dst];
+    P.alpha = al[i];
+    P.beta = (i == 1) ? 0.0 : be[i];
+    P.gamma = c;
+    P.Bn_hi = Yh + bout * b_elems;
+    P.Bn_lo = Yl + bout * b_elems;
+    P.write_next = i < dmax;
+    P.err = w.err;
+    const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols - 1) / 128 - j0 / 128 + 1), 1);
+    mixed_filter_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->ah, maps->al, maps->bh[bin],
+                                                           maps->bl[bin], P);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
+  }
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  if (herr != 0) {
+    fprintf(stderr, "[chase] tensor-core filter: pipeline wait expired (code %d)\n", herr);
+    return CHASE_ERR_CUDA;
+  }
+  return CHASE_OK;
+}
+
 }  // namespace chase

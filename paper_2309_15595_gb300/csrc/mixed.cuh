@@ -9,9 +9,10 @@ namespace chase {
 struct MixedWork {
   void* Ahi = nullptr;   // planar BF16 hi/lo copies of A (see mixed.cu)
   void* Alo = nullptr;
-  void* Yhi = nullptr;   // planar BF16 hi/lo copies of the filter operand
+  void* Yhi = nullptr;   // planar BF16 hi/lo copies of the filter operand (2 buffers)
   void* Ylo = nullptr;
-  const void* A_src = nullptr;  // A the split copies were made from
+  void* maps = nullptr;  // TMA tensor maps of the planes (pinned host)
+  int* err = nullptr;    // device: nonzero when a pipeline wait expired
   int64_t N = 0, ne = 0;
 };
 
