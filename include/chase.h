@@ -172,6 +172,29 @@ CHASE_API int chase_residuals(struct chase_ctx* ctx, const chase_c128* A, int64_
                     const chase_c128* V, int64_t ldv, const double* ritz,
                     int64_t ncols, double* resid);
 
+/* Residual norms exactly like chase_residuals (same kernels, same results), for
+ * callers that cannot allocate device memory and so cannot create a context:
+ * code that lives inside another framework's memory budget (a caching allocator
+ * or pool that owns the device memory) or that must not trigger the
+ * device-wide synchronisation that cudaMalloc/cudaFree can imply. It needs no
+ * chase_ctx and calls no allocating routine. The paper has no counterpart to
+ * this entry point.
+ *   A (N x N, lda >= N), V (N x ncols, ldv >= N), ritz, resid: device pointers
+ *   owned by the caller, as for chase_residuals; stream: a cudaStream_t or NULL.
+ * Scratch: a fixed 4 MiB array of doubles in the library's device memory
+ * (every GPU that loads the library holds it until the process exits); the
+ * call needs ceil(N/64) * ncols doubles of it and returns CHASE_ERR_INVALID_ARG
+ * (with a message on stderr) above that, e.g. ncols > 1675 at N = 20000.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture. All calls
+ * share the one array: calls whose kernels overlap on the GPU (different
+ * streams or host threads) race and give wrong results. Nothing in the array
+ * needs to start at zero; each call writes every partial it reads. Returns
+ * after enqueueing on `stream`. */
+CHASE_API int chase_residuals_noalloc(const chase_c128* A, int64_t lda, const chase_c128* V,
+                                      int64_t ldv, const double* ritz, int64_t N, int64_t ncols,
+                                      double* resid, void* stream);
+
 /* Alg. 5 condition estimate, host arithmetic on host arrays in the solver's
  * current column order: t' = (ritz[0]-c)/e, t = (ritz[locked]-c)/e,
  * cond = |rho(t)|^d |rho(t')|^(d_M - d), d = degs[locked],
