@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="C2")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--N", type=int, default=0, help="override the workload's order (profiling)")
+    ap.add_argument("--nev", type=int, default=0)
+    ap.add_argument("--nex", type=int, default=-1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -106,6 +109,23 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# --------------------------------------------------------------- replicas
+def aggregate_over_ranks(ms_local, steps, dist=None, device=None):
+    """Whole-job throughput of N independent replicas: the timed region is the
+    slowest rank's (max over ranks); value = N * steps / max seconds.
+    Returns (value, max_ms, world)."""
+    import torch
+
+    world = 1
+    ms = float(ms_local)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device or "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * steps / (ms / 1000.0), ms, world
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_sample(A, V0, p, deg, ncols=128):
     """Times the oracle on a bounded sample of one ChASE iteration at full N and
@@ -154,13 +174,26 @@ def build_matrix_host(p):
     return p.matrix()
 
 
-def run_reference(args):
+def make_problem(args):
     from synth import config_problem
 
+    over = {}
+    if args.N:
+        over["N"] = args.N
+    if args.nev:
+        over["nev"] = args.nev
+    if args.nex >= 0:
+        over["nex"] = args.nex
+    p = config_problem(args.config, **over)
+    name = args.config if not over else f"{args.config}-like ({', '.join(f'{k}={v}' for k, v in over.items())})"
+    return p, name
+
+
+def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    p = config_problem(args.config)
+    p, name = make_problem(args)
     A = build_matrix_host(p)
     V0 = p.start_block()
     cores = os.cpu_count()
@@ -178,7 +211,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * t_iter, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: " + workload_desc(p, 20), "N": p.N,
+        "config": {"workload": f"{name}: " + workload_desc(p, 20), "N": p.N,
                    "nev": p.nev, "nex": p.nex, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": "ChASE iterations/s", "cores": cores,
                          "kind": "oracle", "sample": desc + f" (measured {meas:.1f} s)"},
@@ -194,7 +227,6 @@ def run_gpu(args):
     import torch
 
     import paper_2309_15595_gb300 as lib
-    from synth import config_problem
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -209,7 +241,7 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    p = config_problem(args.config)
+    p, name = make_problem(args)
     N, ne = p.N, p.ne
     prec = lib.CHASE_FP64 if args.precision == "fp64" else lib.CHASE_MIXED_BF16X3
     params = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec)
@@ -244,13 +276,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms, world = aggregate_over_ranks(ev0.elapsed_time(ev1), args.steps, dist, dev)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
 
     # dominant kernel: the filter GEMM (deg launches per iteration at iteration 1,
     # all ne vectors active); per-launch time from the library's CUDA events on
@@ -268,7 +295,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lib.CHASE_FP64 else "bf16x3+f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: " + workload_desc(p, deg), "N": N, "nev": p.nev,
+        "config": {"workload": f"{name}: " + workload_desc(p, deg), "N": N, "nev": p.nev,
                    "nex": p.nex, "deg": deg, "precision": args.precision,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * N * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -315,12 +342,8 @@ def run_gpu(args):
             step_e2e()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        line["e2e"] = {"value": world * args.steps / (ems / 1000.0), "unit": "ChASE iterations/s",
+        e2e_value, _, _ = aggregate_over_ranks(e0.elapsed_time(e1), args.steps, dist, dev)
+        line["e2e"] = {"value": e2e_value, "unit": "ChASE iterations/s",
                        "h2d_bytes_per_step": 16 * (N * N + N * ne + N * Q0d.shape[1]),
                        "d2h_bytes_per_step": 16 * N * ne + 16 * ne}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
