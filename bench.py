@@ -52,9 +52,15 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="C2")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-tensor", type=int, default=0, choices=[0, 1],
+                    help="1: FP64 N x N products on the tensor cores (exact digit slicing)")
     ap.add_argument("--N", type=int, default=0, help="override the workload's order (profiling)")
     ap.add_argument("--nev", type=int, default=0)
     ap.add_argument("--nex", type=int, default=-1)
+    ap.add_argument("--tts", default="",
+                    help="comma list of modes (fp64, fp64t, mixed, mixedt) for full solves to "
+                         "resid <= tol instead of the per-iteration step")
+    ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -252,7 +258,8 @@ def run_gpu(args):
     p, name = make_problem(args)
     N, ne = p.N, p.ne
     prec = lib.CHASE_FP64 if args.precision == "fp64" else lib.CHASE_MIXED_BF16X3
-    params = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec)
+    params = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec,
+                                fp64_tensor=args.fp64_tensor)
     deg = int(params.deg_init)
     Ad = p.matrix_torch(dev)
     V0d = lib.colmajor(torch.from_numpy(p.start_block()).to(dev))
@@ -294,7 +301,16 @@ def run_gpu(args):
     launch_ms = ms_filter / deg
     flops_launch = 8.0 * N * N * ne
     achieved = flops_launch / (launch_ms / 1000.0) / 1e12
-    if prec == lib.CHASE_FP64:
+    if prec == lib.CHASE_FP64 and args.fp64_tensor:
+        # issued tensor work: 15 BF16 digit-pair products per real MAC of the planar GEMM
+        issued = 15.0 * flops_launch / (launch_ms / 1000.0) / 1e12
+        peak = measured_bf16_peak()
+        roof = {"kernel": "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)",
+                "bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
+                "frac": issued / peak, "traffic": None, "launches_per_step": deg,
+                "flops_per_launch": 15.0 * flops_launch, "fp64_equivalent_tflops": achieved,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    elif prec == lib.CHASE_FP64:
         roof = {"kernel": "zgemm_kernel<EPI_FILTER> (filter HEMM, Eq. 1)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -310,16 +326,19 @@ def run_gpu(args):
                 "flops_per_launch": 3.0 * flops_launch,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
     phases = {k: sum(s[k] for s in stats) / len(stats) for k in
-              ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid", "ms_total")}
+              ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid", "ms_total")}
+    phases["heev_sweeps"] = stats[-1]["heev_sweeps"]
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     line = {
         "metric": METRIC, "value": value, "unit": "ChASE iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == lib.CHASE_FP64 else "bf16x3+f64", "data": "synthetic",
+        "dtype": ("f64 (bf16 digit slices, exact accumulation)" if args.fp64_tensor else "f64")
+                 if prec == lib.CHASE_FP64 else "bf16x3+f64", "data": "synthetic",
         "config": {"workload": f"{name}: " + workload_desc(p, deg), "N": N, "nev": p.nev,
                    "nex": p.nex, "deg": deg, "precision": args.precision,
+                   "fp64_tensor": args.fp64_tensor,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * N * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
@@ -379,10 +398,64 @@ def run_gpu(args):
     return 0
 
 
+def run_tts(args):
+    """Time-to-solution: full chase_solve runs to resid <= tol per precision mode
+    (fp64 = DFMA products, fp64t = tensor-core FP64 products, mixed = split-BF16x3
+    filter then DFMA, mixedt = split-BF16x3 filter then tensor-core FP64), each
+    checked against the exactly known spectrum and by recomputing residuals."""
+    import torch
+
+    import paper_2309_15595_gb300 as lib
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p, name = make_problem(args)
+    N, ne = p.N, p.ne
+    Ad = p.matrix_torch(dev)
+    V0d = lib.colmajor(torch.from_numpy(p.start_block()).to(dev))
+    Q0d = lib.colmajor(torch.from_numpy(p.lanczos_start()).to(dev))
+    lam = torch.from_numpy(p.eigenvalues()[:p.nev]).to(dev)
+    nrm = p.norm2()
+    modes = {"fp64": (lib.CHASE_FP64, 0), "fp64t": (lib.CHASE_FP64, 1),
+             "mixed": (lib.CHASE_MIXED_BF16X3, 0), "mixedt": (lib.CHASE_MIXED_BF16X3, 1)}
+    out = {}
+    for m in [x for x in args.tts.split(",") if x]:
+        prec, t = modes[m]
+        prm = lib.default_params(N, p.nev, p.nex, precision=prec, fp64_tensor=t,
+                                 max_iter=args.max_iter)
+        V = lib.colmajor(V0d.clone())
+        ritz = torch.zeros(ne, dtype=torch.float64, device=dev)
+        resid = torch.zeros_like(ritz)
+        with lib.Context(prm) as ctx:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        X = V[:, :p.nev]
+        R = Ad @ X - X * ritz[:p.nev].unsqueeze(0)
+        res = (torch.linalg.vector_norm(R, dim=0) / nrm).max().item()
+        err = ((ritz[:p.nev] - lam).abs().max() / nrm).item()
+        out[m] = {"time_to_solution_s": wall, "status": st["status"], "iters": st["iters"],
+                  "matvecs": st["matvecs"], "matvecs_mixed": st["matvecs_mixed"],
+                  "switch_iter": st["switch_iter"], "max_rel_resid": res,
+                  "max_rel_eig_err": err, "phase_ms": {k: st[k] for k in (
+                      "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid")}}
+        print(json.dumps({"mode": m, **out[m]}), file=sys.stderr, flush=True)
+    line = {"metric": METRIC, "kind": "time-to-solution", "unit": "s", "higher_is_better": False,
+            "config": {"workload": f"{name}: {p.spectrum} spectrum, N={N}, nev={p.nev}, "
+                                   f"nex={p.nex}, tol {1e-10}"},
+            "modes": out, "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.tts:
+        return run_tts(args)
     return run_gpu(args)
 
 

@@ -73,7 +73,7 @@ typedef struct chase_c128 { double re, im; } chase_c128;
 typedef struct chase_params {
   int64_t N;              /* matrix order, >= 2 */
   int64_t nev;            /* wanted eigenpairs, >= 1 */
-  int64_t nex;            /* extra search vectors, >= 0; nev + nex <= N */
+  int64_t nex;            /* extra search vectors, >= 0; nev + nex <= min(N, 7168) */
   int32_t deg_init;       /* first-iteration filter degree (20, Section 4.2), even */
   int32_t deg_max;        /* degree cap (36, Section 4.2) */
   int32_t deg_extra;      /* safety margin added by degreeOpt (2) */
@@ -84,7 +84,9 @@ typedef struct chase_params {
   int32_t precision;      /* CHASE_FP64 or CHASE_MIXED_BF16X3 */
   int32_t scaled_filter;  /* 1: filter normalised at mu_1 (default); 0: plain
                              T_m((A - cI)/e) recurrence */
-  int32_t reserved;
+  int32_t fp64_tensor;    /* 1: the FP64 N x N products (filter in FP64, Rayleigh-Ritz
+                             A Q, residual A V) run on the BF16 tensor cores with
+                             exact digit slicing (FP64-class accuracy); 0: DFMA */
   double tol;             /* residual tolerance relative to ||A|| (1e-10, Section 4) */
   double switch_tol;      /* mixed -> FP64 switch, relative residual (1e-5) */
 } chase_params;
@@ -100,6 +102,9 @@ typedef struct chase_stats {
   int32_t qr_variant_count[5];  /* index = CHASE_QR_* */
   int32_t switch_iter;    /* iteration at which the filter became FP64 (0: never mixed) */
   int64_t kernel_launches;  /* kernels this library launched during the solve */
+  int32_t heev_sweeps;    /* Jacobi sweeps summed over the solve's Rayleigh-Ritz steps */
+  int32_t reserved2;
+  double ms_heev;         /* part of ms_rr spent in the Jacobi eigensolver */
 } chase_stats;
 
 /* Fills *p with the defaults above for the given sizes. Host only. */

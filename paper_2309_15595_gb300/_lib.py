@@ -36,7 +36,7 @@ class ChaseParams(ctypes.Structure):
         ("deg_extra", ctypes.c_int32), ("deg_opt", ctypes.c_int32),
         ("max_iter", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
         ("lanczos_vecs", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("scaled_filter", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("scaled_filter", ctypes.c_int32), ("fp64_tensor", ctypes.c_int32),
         ("tol", ctypes.c_double), ("switch_tol", ctypes.c_double),
     ]
 
@@ -54,6 +54,8 @@ class ChaseStats(ctypes.Structure):
         ("qr_variant_count", ctypes.c_int32 * 5),
         ("switch_iter", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64),
+        ("heev_sweeps", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("ms_heev", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

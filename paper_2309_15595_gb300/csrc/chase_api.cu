@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "mixed.cuh"
+#include "ozaki.cuh"
 
 using namespace chase;
 
@@ -43,6 +44,9 @@ struct chase_ctx {
   JacobiWork jw{};
   LanczosWork lw{};
   MixedWork mw{};
+  OzakiWork ow{};
+  double* oz_partial = nullptr;  // residual partials of the tensor-core path (32-row tiles)
+  bool oz_a_valid = false;       // digits of the current solve's A are prepared
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -99,12 +103,14 @@ struct PhaseTimer {
 void free_ctx(chase_ctx* c) {
   if (!c) return;
   void* bufs[] = {c->V2, c->W, c->G, c->Yeig, c->gram_ws, c->dinv, c->info, c->resid_partial,
-                  c->dscal, c->perm_d, c->jw.Gw, c->jw.Zw, c->jw.params, c->jw.red,
+                  c->dscal, c->perm_d, c->jw.Gw, c->jw.Gw2, c->jw.Zw, c->jw.params, c->jw.red,
                   c->lw.Q, c->lw.ws, c->lw.red, c->lw.ab, c->lw.T, c->lw.theta, c->lw.Z,
                   c->lw.out4, c->lw.status};
   for (void* b : bufs)
     if (b) cudaFree(b);
   mixed_free(c->mw);
+  ozaki_free(c->ow);
+  if (c->oz_partial) cudaFree(c->oz_partial);
   if (c->host) cudaFreeHost(c->host);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -114,6 +120,9 @@ void free_ctx(chase_ctx* c) {
 int validate_params(const chase_params* p) {
   if (!p) return CHASE_ERR_INVALID_ARG;
   if (p->N < 2 || p->nev < 1 || p->nex < 0 || p->nev + p->nex > p->N) return CHASE_ERR_INVALID_ARG;
+  // the Jacobi round kernel keeps two columns of the (nev+nex)^2 Rayleigh-Ritz
+  // matrix in shared memory: 32 (nev+nex) bytes <= 227 KB
+  if (p->nev + p->nex > 7168) return CHASE_ERR_INVALID_ARG;
   if (p->deg_init < 2 || (p->deg_init & 1) || p->deg_max < 2 || p->deg_extra < 0)
     return CHASE_ERR_INVALID_ARG;
   if (p->max_iter < 1 || !(p->tol > 0.0) || !(p->switch_tol > 0.0)) return CHASE_ERR_INVALID_ARG;
@@ -121,12 +130,20 @@ int validate_params(const chase_params* p) {
     return CHASE_ERR_INVALID_ARG;
   if (p->lanczos_vecs < 1 || p->lanczos_vecs > 8) return CHASE_ERR_INVALID_ARG;
   if (p->precision != CHASE_FP64 && p->precision != CHASE_MIXED_BF16X3) return CHASE_ERR_INVALID_ARG;
+  if (p->fp64_tensor != 0 && p->fp64_tensor != 1) return CHASE_ERR_INVALID_ARG;
   return CHASE_OK;
 }
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+// Digits of A for the tensor-core FP64 products (once per solve, else per call).
+int prepare_a(chase_ctx* c, const double2* A, int64_t lda) {
+  if (!c->p.fp64_tensor || c->oz_a_valid) return CHASE_OK;
+  CK(ozaki_prepare_a(c->stream, A, lda, c->ow));
+  return CHASE_OK;
 }
 
 // ------------------------------------------------------------------ filter
@@ -160,6 +177,24 @@ int filter_impl(chase_ctx* c, const double2* A, int64_t lda, double2* V, int64_t
                         c->W, c->N, c->mw);
   double2* buf[2] = {V, c->W};
   const int64_t ld[2] = {ldv, c->N};
+  if (c->p.fp64_tensor) {
+    RC(prepare_a(c, A, lda));
+    for (int i = 1; i <= dmax; ++i) {
+      const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
+      const int s = (i - 1) & 1, d = i & 1;
+      Epilogue ep{};
+      ep.mode = EPI_FILTER;
+      ep.alpha = al[i];
+      ep.beta = (i == 1) ? 0.0 : be[i];
+      ep.gamma = cc;
+      ep.X = buf[s];
+      ep.ldx = ld[s];
+      ep.Y = buf[d];
+      ep.ldy = ld[d];
+      CK(ozaki_gemm(c->stream, ncols, j0, buf[s], ld[s], ep, c->ow));
+    }
+    return ozaki_check(c->stream, c->ow);
+  }
   for (int i = 1; i <= dmax; ++i) {
     const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
     const int64_t nact = ncols - j0;
@@ -235,17 +270,41 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
 // ----------------------------------------------------------- Rayleigh-Ritz
 // Q (N x n, ldq) orthonormal, not aliasing V. V[:, 0:n] = Q Y, ritz = eigenvalues.
 int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64_t ldq,
-            double2* V, int64_t ldv, int64_t n, double* ritz) {
+            double2* V, int64_t ldv, int64_t n, double* ritz, chase_stats* st = nullptr) {
   Epilogue ep{};
   ep.mode = EPI_STORE;
   ep.Y = c->W;
   ep.ldy = c->N;
-  CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, Q, ldq, ep));                    // W = A Q
+  if (c->p.fp64_tensor) {                                                        // W = A Q
+    RC(prepare_a(c, A, lda));
+    CK(ozaki_gemm(c->stream, n, 0, Q, ldq, ep, c->ow));
+  } else {
+    CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, Q, ldq, ep));
+  }
   CK(zgram(c->stream, c->N, n, n, Q, ldq, c->W, c->N, c->G, c->ne, false, c->gram_ws,
            c->gram_ws_elems));                                                   // G = Q^H W
   CK(hermitian_part(c->stream, n, c->G, c->ne));
   int sweeps = 0;
-  RC(jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps));
+  {
+    cudaEvent_t h0 = nullptr, h1 = nullptr;
+    if (st) {
+      cudaEventCreate(&h0);
+      cudaEventCreate(&h1);
+      cudaEventRecord(h0, c->stream);
+    }
+    const int rc = jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps);
+    if (st) {
+      cudaEventRecord(h1, c->stream);
+      cudaEventSynchronize(h1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, h0, h1);
+      st->ms_heev += ms;
+      st->heev_sweeps += sweeps;
+      cudaEventDestroy(h0);
+      cudaEventDestroy(h1);
+    }
+    RC(rc);
+  }
   Epilogue e2{};
   e2.mode = EPI_STORE;
   e2.Y = V;
@@ -262,6 +321,13 @@ int resid_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* V, in
   ep.X = V;
   ep.ldx = ldv;
   ep.theta = ritz;
+  if (c->p.fp64_tensor) {
+    RC(prepare_a(c, A, lda));
+    ep.partial = c->oz_partial;
+    CK(ozaki_gemm(c->stream, n, 0, V, ldv, ep, c->ow));
+    CK(resid_reduce(c->stream, c->oz_partial, cdiv(c->N, 32), n, resid));
+    return ozaki_check(c->stream, c->ow);
+  }
   ep.partial = c->resid_partial;
   CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, V, ldv, ep));
   CK(resid_reduce(c->stream, c->resid_partial, zgemm_row_tiles(c->N), n, resid));
@@ -373,9 +439,10 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->dscal, 16));
   A(dalloc(&c->perm_d, (size_t)ne));
   A(dalloc(&c->jw.Gw, (size_t)ne * ne));
+  A(dalloc(&c->jw.Gw2, (size_t)ne * ne));
   A(dalloc(&c->jw.Zw, (size_t)ne * ne));
   A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
-  A(dalloc(&c->jw.red, 1024));
+  A(dalloc(&c->jw.red, std::max<size_t>(1024, jacobi_red_elems())));
   c->jw.nmax = ne;
   A(dalloc(&c->lw.Q, (size_t)3 * N * 8));
   A(dalloc(&c->lw.ws, skinny_workspace_elems(N, 8)));
@@ -387,6 +454,10 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->lw.out4, 4));
   A(dalloc(&c->lw.status, 4));
   if (ok && p->precision == CHASE_MIXED_BF16X3) A(mixed_alloc(c->mw, N, ne));
+  if (ok && p->fp64_tensor) {
+    A(ozaki_alloc(c->ow, N, ne));
+    if (ok) A(dalloc(&c->oz_partial, (size_t)cdiv(N, 32) * ne));
+  }
   if (ok) A(cudaMallocHost(reinterpret_cast<void**>(&c->host), (2 * ne + 16) * sizeof(double)));
   if (ok) A(cudaEventCreate(&c->ev0));
   if (ok) A(cudaEventCreate(&c->ev1));
@@ -494,6 +565,15 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   st.mu_ne = mu_ne;
   st.norm_est = norm_est;
   const double tol_abs = P.tol * norm_est;
+  if (P.fp64_tensor) {  // digits of A once for every tensor-core FP64 product of this solve
+    c->oz_a_valid = false;
+    RC(prepare_a(c, A, lda));
+    c->oz_a_valid = true;
+  }
+  struct ResetDigits {
+    chase_ctx* c;
+    ~ResetDigits() { c->oz_a_valid = false; }
+  } reset_digits{c};
 
   std::vector<int32_t> degs(ne, P.deg_init);
   std::vector<double> rz(ne, 0.0), rs(ne, 0.0);
@@ -569,7 +649,8 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
     if (variant >= 1 && variant <= 4) st.qr_variant_count[variant]++;
     {
       PhaseTimer tm(c, &st.ms_rr);
-      RC(rr_impl(c, A, lda, c->V2 + locked * N, N, C + locked * ldv, ldv, nact, ritz + locked));
+      RC(rr_impl(c, A, lda, c->V2 + locked * N, N, C + locked * ldv, ldv, nact, ritz + locked,
+                 &st));
       CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
     }
     {

@@ -100,6 +100,7 @@ cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, 
 // into Z (n x n, ldz). *sweeps_out (host) and the status.
 struct JacobiWork {
   double2* Gw;       // n x n working copy (ld n)
+  double2* Gw2;      // second buffer: rounds alternate between Gw and Gw2
   double2* Zw;       // n x n unsorted eigenvectors (ld n)
   double* params;    // 4 per pair
   double* red;       // reduction scratch
@@ -107,6 +108,7 @@ struct JacobiWork {
   int64_t nmax;
 };
 size_t jacobi_params_elems(int64_t n);
+size_t jacobi_red_elems();  // doubles of JacobiWork::red
 int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
                 int64_t ldz, JacobiWork& wk, int* sweeps_out);
 // Batched small Jacobi (n <= 64) on `batch` column-major n x n matrices with

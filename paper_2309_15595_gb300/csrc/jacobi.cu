@@ -10,6 +10,7 @@
 // rotate, so each round holds n/2 disjoint pairs that are rotated in parallel
 // and n - 1 rounds visit every pair once (one sweep).
 #include <algorithm>
+#include <cstdio>
 
 #include "common.cuh"
 
@@ -17,6 +18,7 @@ namespace chase {
 namespace {
 
 constexpr int kMaxSweeps = 40;
+constexpr int kCoopMaxGrid = 2048;  // reduction scratch holds 2 * kCoopMaxGrid partials
 
 struct Rot {
   double c, s, px, py, app, aqq;  // px + i py = phi
@@ -194,85 +196,193 @@ __global__ void init_kernel(int64_t n, const double2* G, int64_t ldg, double2* G
   Zw[i + j * n] = make_double2(i == j ? 1.0 : 0.0, 0.0);
 }
 
-__global__ void __launch_bounds__(LJ_T)
-    col_round_kernel(int64_t n, int m, int round, double2* Gw, double2* Zw, double* params) {
-  __shared__ Rot r;
+// Pair k of round `round`, G double-buffered: the owner of pair (p, q) writes
+// the new columns p, q of J^H G J into Gnew, reading only the pre-round Gold,
+// so owners never race. Its column rotation J_k mixes columns p and q row by
+// row; then every pair's row rotation J_k'^H (each thread derives its pairs'
+// rotations from Gold itself) mixes rows (p', q') of these two columns. Z is
+// updated in place: its columns p, q belong to this owner alone.
+__device__ void process_pair(int64_t n, int m, int round, int k, const double2* __restrict__ Gold,
+                             double2* __restrict__ Gnew, double2* __restrict__ Zw, double2* colbuf) {
   int p, q;
-  rr_pair(m, round, blockIdx.x, p, q);
-  if (q >= n) return;
-  if (threadIdx.x == 0) {
-    r = make_rot(Gw[p + p * n].x, Gw[q + q * n].x, Gw[p + (int64_t)q * n]);
-    double* pp = params + 8 * blockIdx.x;
-    pp[0] = r.c; pp[1] = r.s; pp[2] = r.px; pp[3] = r.py; pp[4] = r.app; pp[5] = r.aqq;
-  }
-  __syncthreads();
-  if (r.s == 0.0) return;
-  double2* gp = Gw + (int64_t)p * n;
-  double2* gq = Gw + (int64_t)q * n;
-  double2* zp = Zw + (int64_t)p * n;
-  double2* zq = Zw + (int64_t)q * n;
+  rr_pair(m, round, k, p, q);
+  // odd n: the pair holding the padding index n has one real column, p, which
+  // still receives every other pair's row rotation
+  const bool single = q >= n;
+  if (single) q = p;
+  double2* gp = colbuf;
+  double2* gq = colbuf + n;
+  const Rot r = single ? make_rot(0.0, 0.0, make_double2(0.0, 0.0))
+                       : make_rot(Gold[p + (int64_t)p * n].x, Gold[q + (int64_t)q * n].x,
+                                  Gold[p + (int64_t)q * n]);
+  const double2* Gp = Gold + (int64_t)p * n;
+  const double2* Gq = Gold + (int64_t)q * n;
+  double2* Zp = Zw + (int64_t)p * n;
+  double2* Zq = Zw + (int64_t)q * n;
   for (int64_t i = threadIdx.x; i < n; i += LJ_T) {
-    double2 a = gp[i], b = gq[i];
+    double2 a = Gp[i], b = Gq[i];
     rot_cols(a, b, r);
     gp[i] = a;
     gq[i] = b;
-    double2 x = zp[i], y = zq[i];
-    rot_cols(x, y, r);
-    zp[i] = x;
-    zq[i] = y;
+    if (r.s != 0.0) {
+      double2 x = Zp[i], y = Zq[i];
+      rot_cols(x, y, r);
+      Zp[i] = x;
+      Zq[i] = y;
+    }
   }
+  __syncthreads();
+  for (int kk = threadIdx.x; kk < m / 2; kk += LJ_T) {
+    int pr, qr;
+    rr_pair(m, round, kk, pr, qr);
+    if (qr >= n) continue;
+    const Rot rk = make_rot(Gold[pr + (int64_t)pr * n].x, Gold[qr + (int64_t)qr * n].x,
+                            Gold[pr + (int64_t)qr * n]);
+    if (rk.s == 0.0) continue;
+    rot_rows(gp[pr], gp[qr], rk);
+    rot_rows(gq[pr], gq[qr], rk);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && r.s != 0.0) {  // exact 2 x 2 block of this pair
+    gp[p] = make_double2(r.app, 0.0);
+    gq[q] = make_double2(r.aqq, 0.0);
+    gp[q] = make_double2(0.0, 0.0);
+    gq[p] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2* Np_ = Gnew + (int64_t)p * n;
+  double2* Nq_ = Gnew + (int64_t)q * n;
+  for (int64_t i = threadIdx.x; i < n; i += LJ_T) {
+    Np_[i] = gp[i];
+    if (!single) Nq_[i] = gq[i];
+  }
+  __syncthreads();  // colbuf is reused by this block's next pair
 }
 
-__global__ void __launch_bounds__(LJ_T)
-    row_round_kernel(int64_t n, int m, int round, double2* Gw, const double* params) {
-  int p, q;
-  rr_pair(m, round, blockIdx.x, p, q);
-  if (q >= n) return;
-  const double* pp = params + 8 * blockIdx.x;
-  Rot r;
-  r.c = pp[0]; r.s = pp[1]; r.px = pp[2]; r.py = pp[3]; r.app = pp[4]; r.aqq = pp[5];
-  if (r.s == 0.0) return;
-  for (int64_t j = threadIdx.x; j < n; j += LJ_T) {
-    double2 a = Gw[p + j * n], b = Gw[q + j * n];
-    rot_rows(a, b, r);
-    Gw[p + j * n] = a;
-    Gw[q + j * n] = b;
-  }
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks are co-resident). The
+// wait is bounded: after 2 s it records status[0] = 1 and returns false.
+__device__ bool grid_sync(unsigned* bar, int* status) {
+  __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    Gw[p + (int64_t)q * n] = make_double2(0.0, 0.0);
-    Gw[q + (int64_t)p * n] = make_double2(0.0, 0.0);
-    Gw[p + (int64_t)p * n] = make_double2(r.app, 0.0);
-    Gw[q + (int64_t)q * n] = make_double2(r.aqq, 0.0);
+    ok_s = 1;
+    volatile unsigned* vgen = bar + 1;
+    __threadfence();
+    const unsigned gen = *vgen;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = gtimer();
+      while (*vgen == gen) {
+        if (*(volatile int*)status != 0) {  // another block gave up: leave at once
+          ok_s = 0;
+          break;
+        }
+        if (gtimer() - t0 > 2000000000ull) {
+          atomicExch(status, 1);
+          ok_s = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)status != 0) ok_s = 0;
   }
+  __syncthreads();
+  return ok_s != 0;
 }
 
-constexpr int RED_BLOCKS = 256;
-__global__ void offnorm_partial_kernel(int64_t n, const double2* Gw, double* red) {
-  __shared__ double so[256], sf[256];
-  const int t = threadIdx.x;
-  double a = 0.0, b = 0.0;
-  const int64_t tot = n * n;
-  for (int64_t e = (int64_t)blockIdx.x * 256 + t; e < tot; e += (int64_t)RED_BLOCKS * 256) {
-    const double v = cabs2(Gw[e]);
-    b += v;
-    if (e % n != e / n) a += v;
-  }
-  so[t] = a;
-  sf[t] = b;
-  __syncthreads();
-  for (int s = 128; s >= 1; s >>= 1) {
-    if (t < s) { so[t] += so[t + s]; sf[t] += sf[t + s]; }
+struct CoopArgs {
+  int64_t n;
+  int m, max_sweeps;
+  double2* G0;
+  double2* G1;
+  double2* Z;
+  double* red;      // 2 * gridDim.x partial sums
+  unsigned* bar;    // barrier counter and generation
+  int* status;      // [0] error, [1] sweeps, [2] converged, [3] result in G1
+};
+
+// The whole cyclic Jacobi in one cooperative launch: per sweep a fixed-order
+// off-norm test (identical in every block, so the decision is uniform), then
+// the m - 1 rounds, each followed by a grid barrier.
+__global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs a) {
+  extern __shared__ double2 colbuf[];
+  __shared__ double so[LJ_T], sf[LJ_T];
+  __shared__ int decide;
+  const int64_t n = a.n;
+  const int npairs = a.m / 2;
+  double2* Gcur = a.G0;
+  double2* Gnxt = a.G1;
+  double off_prev = 1e300;
+  int sweep = 0;
+  bool conv = false, alive = true;
+  for (; sweep <= a.max_sweeps && alive; ++sweep) {
+    // off-norm and Frobenius norm of Gcur: block partials, then every block
+    // sums all partials in the same order
+    double o = 0.0, f = 0.0;
+    const int64_t tot = n * n;
+    for (int64_t e = (int64_t)blockIdx.x * LJ_T + threadIdx.x; e < tot; e += (int64_t)gridDim.x * LJ_T) {
+      const double v = cabs2(Gcur[e]);
+      f += v;
+      if (e % n != e / n) o += v;
+    }
+    so[threadIdx.x] = o;
+    sf[threadIdx.x] = f;
     __syncthreads();
+    for (int w = LJ_T / 2; w >= 1; w >>= 1) {
+      if (threadIdx.x < w) {
+        so[threadIdx.x] += so[threadIdx.x + w];
+        sf[threadIdx.x] += sf[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      a.red[blockIdx.x] = so[0];
+      a.red[gridDim.x + blockIdx.x] = sf[0];
+    }
+    if (!grid_sync(a.bar, a.status)) { alive = false; break; }
+    if (threadIdx.x == 0) {
+      double to = 0.0, tf = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) {
+        to += a.red[b];
+        tf += a.red[gridDim.x + b];
+      }
+      const double off = sqrt(to), fro = sqrt(tf);
+      int d = 0;
+      if (off == 0.0 || off <= 1e-15 * fro || (off <= 1e-12 * fro && off > 0.25 * off_prev)) d = 1;
+      else if (sweep == a.max_sweeps) d = 2;
+      off_prev = off;
+      decide = d;
+    }
+    __syncthreads();
+    // every block has read the partials before any block rewrites them
+    if (!grid_sync(a.bar, a.status)) { alive = false; break; }
+    if (decide == 1) { conv = true; break; }
+    if (decide == 2) break;
+    for (int round = 0; round < a.m - 1; ++round) {
+      for (int k = blockIdx.x; k < npairs; k += gridDim.x)
+        process_pair(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf);
+      if (!grid_sync(a.bar, a.status)) { alive = false; break; }
+      double2* t = Gcur;
+      Gcur = Gnxt;
+      Gnxt = t;
+    }
   }
-  if (t == 0) { red[blockIdx.x] = so[0]; red[RED_BLOCKS + blockIdx.x] = sf[0]; }
-}
-__global__ void offnorm_final_kernel(const double* red, double* out2) {
-  if (threadIdx.x != 0) return;
-  double a = 0.0, b = 0.0;
-  for (int i = 0; i < RED_BLOCKS; ++i) { a += red[i]; b += red[RED_BLOCKS + i]; }
-  out2[0] = sqrt(a);
-  out2[1] = sqrt(b);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.status[1] = sweep;
+    a.status[2] = conv ? 1 : 0;
+    a.status[3] = Gcur == a.G1 ? 1 : 0;
+  }
 }
 
 __global__ void rank_kernel(int64_t n, const double2* Gw, double* w, int* rank) {
@@ -299,7 +409,9 @@ bool g_small_attr = false;
 
 }  // namespace
 
-size_t jacobi_params_elems(int64_t n) { return (size_t)8 * (n / 2 + 2) + 2 * RED_BLOCKS + 8 + n; }
+size_t jacobi_red_elems() { return (size_t)2 * kCoopMaxGrid + 16; }
+
+size_t jacobi_params_elems(int64_t n) { return (size_t)8 * (n / 2 + 2) + 8 + n; }
 
 cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2* G, double* w,
                                  double2* Z, int* status) {
@@ -318,7 +430,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
                 int64_t ldz, JacobiWork& wk, int* sweeps_out) {
   if (n <= 0) return CHASE_OK;
   cudaError_t e;
-  int* status = reinterpret_cast<int*>(wk.red + 2 * RED_BLOCKS + 4);
+  int* status = reinterpret_cast<int*>(wk.red + 2 * kCoopMaxGrid + 8);
   if (n <= SJ_MAX) {
     // pack G (ld n) into Gw, run the single-CTA kernel into Zw, copy to Z.
     e = cudaMemsetAsync(status, 0, sizeof(int), s);
@@ -335,37 +447,61 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return CHASE_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CHASE_ERR_CUDA;
-    if (sweeps_out) *sweeps_out = -1;
+    if (sweeps_out) *sweeps_out = 0;
     return hs ? CHASE_ERR_HEEV_NOCONV : CHASE_OK;
   }
   const int m = (int)(n + (n & 1));
   const int npairs = m / 2;
-  init_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, G, ldg, wk.Gw, wk.Zw); count_launch();
-  if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
-  double off_prev = 1e300;
-  bool conv = false;
-  int sweep = 0;
-  for (; sweep <= kMaxSweeps; ++sweep) {
-    offnorm_partial_kernel<<<RED_BLOCKS, 256, 0, s>>>(n, wk.Gw, wk.red); count_launch();
-    offnorm_final_kernel<<<1, 32, 0, s>>>(wk.red, wk.red + 2 * RED_BLOCKS); count_launch();
-    e = cudaMemcpyAsync(wk.host_red, wk.red + 2 * RED_BLOCKS, 2 * sizeof(double),
-                        cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CHASE_ERR_CUDA;
-    const double off = wk.host_red[0], fro = wk.host_red[1];
-    if (off == 0.0 || off <= 1e-15 * fro || (off <= 1e-12 * fro && off > 0.25 * off_prev)) {
-      conv = true;
-      break;
-    }
-    off_prev = off;
-    if (sweep == kMaxSweeps) break;
-    for (int round = 0; round < m - 1; ++round) {
-      col_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.Zw, wk.params); count_launch();
-      row_round_kernel<<<npairs, LJ_T, 0, s>>>(n, m, round, wk.Gw, wk.params); count_launch();
-    }
-    if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
+  const size_t smem = (size_t)2 * n * sizeof(double2);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, LJ_T, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return CHASE_ERR_CUDA;
+  const int grid = std::min(std::min(npairs, per_sm * nsm), kCoopMaxGrid);
+  double2* Gcur = wk.Gw;
+  init_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, G, ldg, Gcur, wk.Zw); count_launch();
+  // barrier words and status live in the reduction scratch after the partials
+  unsigned* bar = reinterpret_cast<unsigned*>(wk.red + 2 * kCoopMaxGrid);
+  int* st = reinterpret_cast<int*>(wk.red + 2 * kCoopMaxGrid + 2);
+  if (cudaMemsetAsync(wk.red + 2 * kCoopMaxGrid, 0, 8 * sizeof(double), s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  CoopArgs args;
+  args.n = n;
+  args.m = m;
+  args.max_sweeps = kMaxSweeps;
+  args.G0 = wk.Gw;
+  args.G1 = wk.Gw2;
+  args.Z = wk.Zw;
+  args.red = wk.red;
+  args.bar = bar;
+  args.status = st;
+  void* kargs[] = {&args};
+  if (cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(LJ_T), kargs,
+                                  smem, s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  count_launch();
+  int hst[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  if (hst[0] != 0) {
+    fprintf(stderr, "[chase] Jacobi: grid barrier wait expired\n");
+    return CHASE_ERR_CUDA;
   }
+  if (hst[3]) Gcur = wk.Gw2;
+  const int sweep = hst[1];
+  const bool conv = hst[2] != 0;
   int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
-  rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, w, rank); count_launch();
+  rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, Gcur, w, rank); count_launch();
   permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, wk.Zw, rank,
                                                                                     Z, ldz); count_launch();
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;

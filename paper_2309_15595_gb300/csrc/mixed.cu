@@ -5,13 +5,16 @@
 // Every real operand x is split into two BF16 planes, hi = bf16(x),
 // lo = bf16(x - hi), and the product uses three MMAs per K block,
 // hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory (split-BF16 x3).
-// The recurrence state stays FP64: the epilogue reads the FP32 tile from TMEM,
-// forms Y_new = alpha (W - c Y_cur) + beta Y_prev in FP64 (Eq. 1), stores it over
-// Y_prev and also writes the BF16 hi/lo planes of Y_new in the K-major layout
-// the next step's MMA reads, so no separate conversion pass runs per degree.
+// The recurrence state is kept in FP32 (its 2^-24 rounding is far below the
+// 2^-15 of the split products, and FP32 math avoids the slow FP64 pipe): the
+// epilogue reads the FP32 tile from TMEM, forms Y_new = alpha (W - c Y_cur) +
+// beta Y_prev (Eq. 1), stores it over Y_prev and also writes the BF16 hi/lo
+// planes of Y_new in the K-major layout the next step's MMA reads, so no
+// separate conversion pass runs per degree. The FP64 input V is converted once
+// before the first step and the result converted back once after the last.
 //
 // Kernel structure (one 128 x 256 output tile per CTA, 6 warps):
-//   warp 0   TMA producer: A_hi, A_lo (128 x 64) and B_hi, B_lo (256 x 64) per
+//   warp 0   TMA producer: A_hi, A_lo (128 x 32) and B_hi, B_lo (256 x 32) per
 //            K block into a 2-stage shared-memory ring (128B swizzle)
 //   warp 1   TMEM allocator and single-thread MMA issuer (tcgen05.mma, M=128,
 //            N=256, K=16, kind::f16 with BF16 inputs)
@@ -30,10 +33,14 @@
 namespace chase {
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 64, STAGES = 2;
-constexpr int A_TILE = TM * TK * 2;                 // 16 KB
-constexpr int B_TILE = TN * TK * 2;                 // 32 KB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;  // 96 KB
+// K block of 32 BF16 (64-byte rows, 64B swizzle) and a 4-stage ring: three
+// stages stay in flight while one is consumed, enough bytes in flight to
+// cover the TMA latency at the MMA rate.
+constexpr int TM = 128, TN = 256, TK = 32, STAGES = 4;
+constexpr int A_TILE = TM * TK * 2;                 // 8 KB
+constexpr int B_TILE = TN * TK * 2;                 // 16 KB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;  // 48 KB
+constexpr int KPAD = 64;                            // K-half padding of the planes
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 256;
@@ -41,11 +48,9 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 struct Params {
   int64_t N, Np, j0, ncols;     // rows, padded K half, first active column, end column
-  const double2* Ycur;
-  int64_t ldc;
-  double2* Yprev;
-  int64_t ldp;
-  double alpha, beta, gamma;
+  const float2* Ycur;           // FP32 recurrence state, ld N
+  float2* Yprev;
+  float alpha, beta, gamma;
   __nv_bfloat16* Bn_hi;         // next-step operand planes (rows = B^T rows, ld = 2 Np)
   __nv_bfloat16* Bn_lo;
   int write_next;
@@ -99,15 +104,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
-// UMMA shared-memory descriptor, K-major operand with the 128-byte swizzle:
-// 8-row x 128-byte atoms, SBO = 1024 B between atoms, version 1 (sm_100+).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+// UMMA shared-memory descriptor, K-major operand with the 64-byte swizzle:
+// 8-row x 64-byte atoms, SBO = 512 B between atoms, version 1 (sm_100+).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset
   d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
   return d;
 }
 // Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M x N.
@@ -148,6 +153,10 @@ __device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat1
   hi = __double2bfloat16(x);
   lo = __double2bfloat16(x - (double)__bfloat162float(hi));
 }
+__device__ __forceinline__ void split2f(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
 
 // B^T row of complex column j: tile j/128 holds 256 rows, real parts first.
 __device__ __forceinline__ int64_t brow_re(int64_t j) { return (j >> 7) * 256 + (j & 127); }
@@ -159,7 +168,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const __grid_constant__ CUtensorMap tmBh,
                         const __grid_constant__ CUtensorMap tmBl, Params P) {
   extern __shared__ uint8_t smem_raw[];
-  // 1024-byte alignment of the shared-window address (128B-swizzle atoms)
+  // 1024-byte alignment of the shared-window address (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready
@@ -232,9 +241,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int kk = 0; kk < TK / 16; ++kk) {
         const uint32_t off = kk * 32;  // 16 BF16 along K
         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        umma_bf16(tmem, sdesc_sw128(ah + off), sdesc_sw128(bh + off), acc0);
-        umma_bf16(tmem, sdesc_sw128(ah + off), sdesc_sw128(bl + off), 1u);
-        umma_bf16(tmem, sdesc_sw128(al + off), sdesc_sw128(bh + off), 1u);
+        umma_bf16(tmem, sdesc_sw64(ah + off), sdesc_sw64(bh + off), acc0);
+        umma_bf16(tmem, sdesc_sw64(ah + off), sdesc_sw64(bl + off), 1u);
+        umma_bf16(tmem, sdesc_sw64(al + off), sdesc_sw64(bh + off), 1u);
       }
       umma_commit(smem_u32(&bars[STAGES + s]));  // stage free once these MMAs finish
     }
@@ -258,21 +267,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int jj = 0; jj < 32; ++jj) {
           const int64_t col = tile * 128 + jc * 32 + jj;
           if (col < P.j0 || col >= P.ncols) continue;
-          const double2 yc = P.Ycur[row + col * P.ldc];
-          double2* yp = P.Yprev + row + col * P.ldp;
-          double vr = P.alpha * ((double)re[jj] - P.gamma * yc.x);
-          double vi = P.alpha * ((double)im[jj] - P.gamma * yc.y);
-          if (P.beta != 0.0) {
-            const double2 y0 = *yp;
-            vr = fma(P.beta, y0.x, vr);
-            vi = fma(P.beta, y0.y, vi);
+          const float2 yc = P.Ycur[row + col * P.N];
+          float2* yp = P.Yprev + row + col * P.N;
+          float vr = P.alpha * fmaf(-P.gamma, yc.x, re[jj]);
+          float vi = P.alpha * fmaf(-P.gamma, yc.y, im[jj]);
+          if (P.beta != 0.0f) {
+            const float2 y0 = *yp;
+            vr = fmaf(P.beta, y0.x, vr);
+            vi = fmaf(P.beta, y0.y, vi);
           }
-          *yp = make_double2(vr, vi);
+          *yp = make_float2(vr, vi);
           if (P.write_next) {
             __nv_bfloat16 rh, rl, ih, il, nh, nl;
-            split2(vr, rh, rl);
-            split2(vi, ih, il);
-            split2(-vi, nh, nl);
+            split2f(vr, rh, rl);
+            split2f(vi, ih, il);
+            split2f(-vi, nh, nl);
             const int64_t br = brow_re(col), bi = br + 128, ld = 2 * P.Np;
             P.Bn_hi[br * ld + row] = rh;
             P.Bn_lo[br * ld + row] = rl;
@@ -325,14 +334,16 @@ __global__ void split_a_kernel(int64_t N, int64_t Np, const double2* __restrict_
   }
 }
 
-// Columns j0..ncols of Y (column-major complex) -> B^T planes (K-major rows).
+// Columns j0..ncols of Y (column-major complex) -> B^T planes (K-major rows)
+// and the FP32 recurrence state S (ld N).
 __global__ void split_y_kernel(int64_t N, int64_t Np, int64_t j0, const double2* __restrict__ Y,
                                int64_t ldy, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo) {
+                               __nv_bfloat16* __restrict__ lo, float2* __restrict__ S) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = j0 + blockIdx.y;
   if (k >= N) return;
   const double2 y = Y[k + j * ldy];
+  S[k + j * N] = make_float2((float)y.x, (float)y.y);
   __nv_bfloat16 rh, rl, ih, il, nh, nl;
   split2(y.x, rh, rl);
   split2(y.y, ih, il);
@@ -346,6 +357,16 @@ __global__ void split_y_kernel(int64_t N, int64_t Np, int64_t j0, const double2*
   lo[bi * ld + k] = il;
   hi[bi * ld + Np + k] = rh;
   lo[bi * ld + Np + k] = rl;
+}
+
+// FP32 state -> FP64 columns of V.
+__global__ void state_to_f64_kernel(int64_t N, const float2* __restrict__ S, double2* __restrict__ V,
+                                    int64_t ldv) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (k >= N) return;
+  const float2 v = S[k + j * N];
+  V[k + j * ldv] = make_double2((double)v.x, (double)v.y);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -369,7 +390,7 @@ bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows
   const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -385,7 +406,7 @@ struct Maps {
 cudaError_t mixed_alloc(MixedWork& w, int64_t N, int64_t ne) {
   w.N = N;
   w.ne = ne;
-  const int64_t Np = cdiv(N, TK) * TK;
+  const int64_t Np = cdiv(N, KPAD) * KPAD;
   const int64_t brows = cdiv(ne, 128) * 256;
   const size_t a_bytes = (size_t)N * 2 * Np * sizeof(__nv_bfloat16);
   const size_t b_bytes = (size_t)brows * 2 * Np * sizeof(__nv_bfloat16);
@@ -410,6 +431,7 @@ cudaError_t mixed_alloc(MixedWork& w, int64_t N, int64_t ne) {
     ok = ok && make_map(&maps->bh[b], yh, brows, Np, TN) && make_map(&maps->bl[b], yl, brows, Np, TN);
   }
   if (!ok) return cudaErrorInvalidValue;
+  if ((e = cudaMalloc(&w.S32, (size_t)2 * N * ne * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMemset(w.err, 0, sizeof(int))) != cudaSuccess) return e;
   return cudaFuncSetAttribute(mixed_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -422,6 +444,7 @@ void mixed_free(MixedWork& w) {
   if (w.Yhi) cudaFree(w.Yhi);
   if (w.Ylo) cudaFree(w.Ylo);
   if (w.err) cudaFree(w.err);
+  if (w.S32) cudaFree(w.S32);
   if (w.maps) cudaFreeHost(w.maps);
   w = MixedWork{};
 }
@@ -432,7 +455,7 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
   if (ncols == 0) return CHASE_OK;
   if (!w.maps || N != w.N || ncols > w.ne) return CHASE_ERR_INVALID_ARG;
   const Maps* maps = static_cast<const Maps*>(w.maps);
-  const int64_t Np = cdiv(N, TK) * TK;
+  const int64_t Np = cdiv(N, KPAD) * KPAD;
   const int64_t brows = cdiv(w.ne, 128) * 256;
   const size_t b_elems = (size_t)brows * 2 * Np;
   __nv_bfloat16* Yh = static_cast<__nv_bfloat16*>(w.Yhi);
@@ -441,29 +464,28 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
   split_a_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(N, 32), 1), dim3(32, 8, 1), 0, s>>>(
       N, Np, A, lda, static_cast<__nv_bfloat16*>(w.Ahi), static_cast<__nv_bfloat16*>(w.Alo));
   count_launch();
+  float2* st[2] = {static_cast<float2*>(w.S32), static_cast<float2*>(w.S32) + (size_t)N * w.ne};
   split_y_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, Np, 0, V, ldv,
-                                                                                   Yh, Yl);
+                                                                                   Yh, Yl, st[0]);
   count_launch();
   if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_ERR_CUDA;
-  double2* buf[2] = {V, W};
-  const int64_t ld[2] = {ldv, ldw};
+  (void)W;
+  (void)ldw;
   const int dmax = degs[ncols - 1];
   for (int i = 1; i <= dmax; ++i) {
     const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
-    const int src = (i - 1) & 1, dst = i & 1;   // FP64 state buffers
+    const int src = (i - 1) & 1, dst = i & 1;   // FP32 state buffers
     const int bin = (i - 1) & 1, bout = i & 1;  // operand plane buffers
     Params P;
     P.N = N;
     P.Np = Np;
     P.j0 = j0;
     P.ncols = ncols;
-    P.Ycur = buf[src];
-    P.ldc = ld[src];
-    P.Yprev = buf[dst];
-    P.ldp = ld[dst];
-    P.alpha = al[i];
-    P.beta = (i == 1) ? 0.0 : be[i];
-    P.gamma = c;
+    P.Ycur = st[src];
+    P.Yprev = st[dst];
+    P.alpha = (float)al[i];
+    P.beta = (i == 1) ? 0.0f : (float)be[i];
+    P.gamma = (float)c;
     P.Bn_hi = Yh + bout * b_elems;
     P.Bn_lo = Yl + bout * b_elems;
     P.write_next = i < dmax;
@@ -474,6 +496,10 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   }
+  // even degrees: every column's final value is in state buffer 0
+  state_to_f64_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, st[0], V,
+                                                                                       ldv);
+  count_launch();
   int herr = 0;
   if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

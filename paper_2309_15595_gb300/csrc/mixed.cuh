@@ -13,6 +13,7 @@ struct MixedWork {
   void* Ylo = nullptr;
   void* maps = nullptr;  // TMA tensor maps of the planes (pinned host)
   int* err = nullptr;    // device: nonzero when a pipeline wait expired
+  void* S32 = nullptr;   // two FP32 recurrence-state buffers, N x ne complex each
   int64_t N = 0, ne = 0;
 };
 

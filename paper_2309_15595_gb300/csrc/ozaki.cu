@@ -1,0 +1,662 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores (error-free splitting in
+// the manner of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), used for the FP64 filter, the
+// Rayleigh-Ritz product A Q and the residual product A V.
+//
+// Same planar real form as the mixed filter: W = [Ar | Ai] [[Yr, Yi], [-Yi, Yr]].
+// The diagonal of A is taken out of the digit planes and applied exactly in
+// FP64 in the epilogue (A_ii B_ij): the row scales then follow the off-diagonal
+// entries, which keeps their relative precision when A is diagonally dominant.
+// Row i of the left operand is scaled by 2^-e_i and column j of the right one
+// by 2^-f_j so every entry x has |x| < 1/2, then cut into S = 5 signed 8-bit
+// digits, x = sum_s d_s 2^-8s + O(2^-40), |d_s| <= 128, computed exactly in
+// FP64; every digit is exact in BF16. The product keeps the 15 digit pairs
+// (s, t) with s + t <= 6; pair (s, t) contributes at weight 2^-8(s+t).
+// Digit products are < 2^14 and exact; the FP32 tensor-memory accumulator of
+// one level L = s + t stays an exact integer over a chunk of 256 K values
+// (at most (L-1) 2^22 <= 2^24 for L <= 5), so after every chunk the epilogue
+// warps move levels 2-5 into exact int64 accumulators (shifted into one common
+// scale, at most 2^55 in total) and add level 6, whose weight is 2^-8 below
+// that scale, rounded to it (error <= 1/2 unit of 2^-40 per chunk).
+// The result is W = 2^(e_i + f_j) acc 2^-40, accurate to a few units of 2^-40
+// relative to |A_i.| |Y_.j| per term: FP64-class.
+//
+// Kernel structure (128 x 96 real output tile = 48 complex columns, 10 warps):
+//   warp 0    TMA producer: 5 A digit tiles (128 x 32) and 5 B digit tiles
+//             (96 x 32) per K block into a 3-stage ring (64B swizzle)
+//   warp 1    TMEM allocator and MMA issuer: 15 tcgen05.mma (M=128, N=96,
+//             K=16) per 16-wide K step, one accumulator per level (5 x 96
+//             TMEM columns); after each 256-wide chunk it hands the
+//             accumulators to the epilogue and waits until they are drained
+//   warps 2-9 epilogue: warp w owns TMEM lane quarter w % 4 and half of the
+//             complex columns; int64/FP32 accumulators in registers; at the
+//             end forms the FP64 result and applies the fused update.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+
+#include "ozaki.cuh"
+
+namespace chase {
+namespace {
+
+constexpr int OS = 5;                    // digits per operand
+constexpr int TM = 128, TN = 96, TK = 32, STAGES = 3;
+constexpr int CHUNK_KB = 8;              // K blocks per exact chunk (256 values)
+constexpr int A_TILE = TM * TK * 2;      // 8 KB per digit
+constexpr int B_TILE = TN * TK * 2;      // 6 KB per digit
+constexpr int STAGE_BYTES = OS * (A_TILE + B_TILE);  // 70 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int NTHREADS = 320;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int KPAD = 128;                // K-half padding: 2 Np is a multiple of 256
+constexpr int HC = TN / 4;               // complex columns per epilogue warp half (24)
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// K-major operand, 64-byte swizzle: 8-row x 64-byte atoms, SBO = 512 B.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+// 16 and 8 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// B^T row of complex column j: tiles of 48 complex columns, 96 rows each,
+// real parts first.
+__device__ __forceinline__ int64_t brow_re(int64_t j) { return (j / 48) * 96 + (j % 48); }
+
+struct Params {
+  int64_t N, Np, j0, ncols;   // rows, padded K half, first active column, end column
+  int64_t brows;              // rows of one B digit plane
+  const int* escale_a;        // per row: exponent e_i
+  const double2* diag;        // diagonal of A, applied exactly in FP64
+  const double2* Bsrc;        // right operand in FP64 (absolute columns, ld ldbs)
+  int64_t ldbs;
+  const int* escale_b;        // per complex column: exponent f_j
+  int mode;                   // EPI_STORE / EPI_FILTER / EPI_RESID
+  double alpha, beta, gamma;  // filter
+  const double2* X;           // filter/resid: B operand in FP64 (ld ldx)
+  int64_t ldx;
+  double2* Y;                 // store/filter destination (ld ldy)
+  int64_t ldy;
+  const double* theta;        // resid
+  double* partial;            // resid: [32-row tile + col * ceil(N / 32)]
+  int* err;
+};
+
+// ---------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // [0,S) full, [S,2S) empty, [2S] accumulators full, [2S+1] accumulators empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TM;
+  const int64_t tile = P.j0 / 48 + blockIdx.y;    // absolute 48-column tile
+  const int nkb = (int)((2 * P.Np) / TK);
+  const int nchunks = nkb / CHUNK_KB;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    mbar_init(smem_u32(&bars[2 * STAGES + 1]), 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------ TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, P.err, 11)) {
+          s_abort = 1;
+          break;
+        }
+        if (*(volatile int*)&s_abort) break;
+        const uint32_t full = smem_u32(&bars[s]);
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(full, STAGE_BYTES);
+        const int kx = kb * TK;
+#pragma unroll
+        for (int d = 0; d < OS; ++d) {
+          // digit planes are stacked along rows: digit d of row r is row d * rows + r
+          tma_load_2d(smem_u32(st + d * A_TILE), &tmA, kx, (int)(d * P.N + m0), full);
+        }
+#pragma unroll
+        for (int d = 0; d < OS; ++d) {
+          tma_load_2d(smem_u32(st + OS * A_TILE + d * B_TILE), &tmB, kx,
+                      (int)(d * P.brows + tile * TN), full);
+        }
+        ++issued;
+      }
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+        mbar_wait(smem_u32(&bars[kb % STAGES]), (uint32_t)(kb / STAGES) & 1u, P.err, 12);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------ MMA issuer
+      int kb = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        if (c > 0 && !mbar_wait(smem_u32(&bars[2 * STAGES + 1]), (uint32_t)(c - 1) & 1u, P.err, 13)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kc = 0; kc < CHUNK_KB; ++kc, ++kb) {
+          const int s = kb % STAGES;
+          const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&bars[s]), ph, P.err, 14) || *(volatile int*)&s_abort) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk) {
+            const uint32_t off = kk * 32;
+#pragma unroll
+            for (int L = 2; L <= OS + 1; ++L) {
+#pragma unroll
+              for (int sa = 1; sa < L; ++sa) {
+                const int tb = L - sa;
+                const uint32_t acc = (kc == 0 && kk == 0 && sa == 1) ? 0u : 1u;
+                umma_bf16(tmem + (uint32_t)((L - 2) * TN),
+                          sdesc_sw64(st + (sa - 1) * A_TILE + off),
+                          sdesc_sw64(st + OS * A_TILE + (tb - 1) * B_TILE + off), acc);
+              }
+            }
+          }
+          umma_commit(smem_u32(&bars[STAGES + s]));
+        }
+        umma_commit(smem_u32(&bars[2 * STAGES]));  // chunk c ready
+      }
+      if (!ok) {
+        s_abort = 1;
+        umma_commit(smem_u32(&bars[2 * STAGES]));
+      }
+    }
+  } else {
+    // ------------------------------------------------------- epilogue warps
+    const int q = warp & 3;                   // TMEM lane quarter
+    const int h = (warp - 2) >> 2;            // complex column half: [h*24, h*24+24)
+    const int64_t row = m0 + q * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    long long acc[2 * HC];                    // re[0..24), im[24..48), weight 2^-40
+#pragma unroll
+    for (int j = 0; j < 2 * HC; ++j) acc[j] = 0;
+    bool go = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), (uint32_t)c & 1u, P.err, 15);
+      go = __all_sync(0xffffffffu, ok && !*(volatile int*)&s_abort);
+      if (!go) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // levels 2..5 are exact integers below 2^24 per chunk: int64 at weight
+      // 2^-40 (level L shifted by 8 (5 - L) bits); level 6 (weight 2^-48) is
+      // rounded to that weight once per chunk (error <= 1/2 unit of 2^-40)
+#pragma unroll
+      for (int L = 2; L <= OS + 1; ++L) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
+          float v[HC];
+          const uint32_t base = tl + (uint32_t)((L - 2) * TN + part * 48 + h * HC);
+          tmem_ld16(base, v);
+          tmem_ld8(base + 16, v + 16);
+          tmem_wait_ld();
+          if (L <= OS) {
+            const int sh = 8 * (OS - L);
+#pragma unroll
+            for (int j = 0; j < HC; ++j)
+              acc[part * HC + j] += (long long)__float2int_rn(v[j]) << sh;
+          } else {
+#pragma unroll
+            for (int j = 0; j < HC; ++j)
+              acc[part * HC + j] += (long long)__float2int_rn(v[j] * 0.00390625f);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * STAGES + 1]));
+    }
+    // ------------------------------------------------ FP64 result + update
+    double rsq[HC];
+    if (go && row < P.N) {
+      const double sa = ldexp(1.0, P.escale_a[row]);
+      const double2 dg = P.diag[row];
+#pragma unroll
+      for (int jj = 0; jj < HC; ++jj) {
+        const int64_t col = tile * 48 + h * HC + jj;
+        rsq[jj] = 0.0;
+        if (col < P.j0 || col >= P.ncols) continue;
+        const double sc = sa * ldexp(1.0, P.escale_b[col]);
+        const double2 b = P.Bsrc[row + col * P.ldbs];
+        const double wr = fma(dg.x, b.x, fma(-dg.y, b.y, sc * ((double)acc[jj] * 0x1p-40)));
+        const double wi = fma(dg.x, b.y, fma(dg.y, b.x, sc * ((double)acc[HC + jj] * 0x1p-40)));
+        if (P.mode == EPI_STORE) {
+          P.Y[row + col * P.ldy] = make_double2(wr, wi);
+        } else if (P.mode == EPI_FILTER) {
+          const double2 x = P.X[row + col * P.ldx];
+          double2* yp = P.Y + row + col * P.ldy;
+          double vr = P.alpha * fma(-P.gamma, x.x, wr);
+          double vi = P.alpha * fma(-P.gamma, x.y, wi);
+          if (P.beta != 0.0) {
+            const double2 y0 = *yp;
+            vr = fma(P.beta, y0.x, vr);
+            vi = fma(P.beta, y0.y, vi);
+          }
+          *yp = make_double2(vr, vi);
+        } else {
+          const double2 x = P.X[row + col * P.ldx];
+          const double th = P.theta[col];
+          const double dx = fma(-th, x.x, wr), dy = fma(-th, x.y, wi);
+          rsq[jj] = fma(dx, dx, dy * dy);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < HC; ++jj) rsq[jj] = 0.0;
+    }
+    if (P.mode == EPI_RESID && go) {
+      // per column: sum over this warp's 32 rows, one partial per 32-row tile
+      const int64_t nt32 = (P.N + 31) / 32;
+      const int64_t t32 = blockIdx.x * 4 + q;
+#pragma unroll
+      for (int jj = 0; jj < HC; ++jj) {
+        double v = rsq[jj];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        const int64_t col = tile * 48 + h * HC + jj;
+        if (lane == 0 && t32 < nt32 && col >= P.j0 && col < P.ncols) P.partial[t32 + col * nt32] = v;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ digit prep
+__device__ __forceinline__ void digits5(double x, __nv_bfloat16* d) {
+  // |x| < 1/2: x = sum_s d_s 2^-8s + r, |d_s| <= 128 (exact in FP64 and BF16)
+#pragma unroll
+  for (int s = 0; s < OS; ++s) {
+    const double r = x * 256.0;
+    const double di = rint(r);
+    d[s] = __double2bfloat16(di);
+    x = r - di;
+  }
+}
+
+__device__ __forceinline__ int scale_exp(double mx) {
+  if (!(mx > 0.0)) return 0;
+  int E;
+  frexp(mx, &E);  // mx = f 2^E, f in [0.5, 1)
+  return E + 1;   // mx 2^-(E+1) in [0.25, 0.5)
+}
+
+// Row maxima of A (column-major): amax[i] = max_k max(|Re A_ik|, |Im A_ik|),
+// as the bit pattern of a non-negative double (monotone in unsigned order).
+__global__ void rowmax_kernel(int64_t N, const double2* __restrict__ A, int64_t lda,
+                              unsigned long long* __restrict__ amax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t k0 = (int64_t)blockIdx.y * 256, k1 = min(N, k0 + 256);
+  double m = 0.0;
+  for (int64_t k = k0; k < k1; ++k) {
+    if (k == i) continue;  // the diagonal is applied separately, exactly
+    const double2 a = A[i + k * lda];
+    m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
+  }
+  atomicMax(&amax[i], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void diag_kernel(int64_t N, const double2* __restrict__ A, int64_t lda,
+                            double2* __restrict__ d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) d[i] = A[i + i * lda];
+}
+
+__global__ void exps_kernel(int64_t n, const unsigned long long* __restrict__ mx, int* __restrict__ e) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) e[i] = scale_exp(__longlong_as_double((long long)mx[i]));
+}
+
+// A -> 5 digit planes, each N rows x 2 Np (row-major [Ar | Ai]), stacked.
+__global__ void slice_a_kernel(int64_t N, int64_t Np, const double2* __restrict__ A, int64_t lda,
+                               const int* __restrict__ ea, __nv_bfloat16* __restrict__ out) {
+  __shared__ double2 tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + tx, k = k0 + r;
+    tile[r][tx] = (i < N && k < N) ? A[i + k * lda] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int64_t ld = 2 * Np;
+  const size_t plane = (size_t)N * ld;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, k = k0 + tx;
+    if (i < N && k < N) {
+      const double2 a = i == k ? make_double2(0.0, 0.0) : tile[tx][r];
+      const double s = ldexp(1.0, -ea[i]);
+      __nv_bfloat16 dr[OS], di[OS];
+      digits5(a.x * s, dr);
+      digits5(a.y * s, di);
+#pragma unroll
+      for (int d = 0; d < OS; ++d) {
+        out[d * plane + i * ld + k] = dr[d];
+        out[d * plane + i * ld + Np + k] = di[d];
+      }
+    }
+  }
+}
+
+// Column maxima of Y (complex columns j0 .. j0 + gridDim.x): one CTA per column.
+__global__ void colexp_kernel(int64_t N, int64_t j0, const double2* __restrict__ Y, int64_t ldy,
+                              int* __restrict__ eb) {
+  __shared__ double red[256];
+  const int64_t j = j0 + blockIdx.x;
+  double m = 0.0;
+  for (int64_t k = threadIdx.x; k < N; k += 256) {
+    const double2 y = Y[k + j * ldy];
+    m = fmax(m, fmax(fabs(y.x), fabs(y.y)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) eb[j] = scale_exp(red[0]);
+}
+
+// Y columns -> 5 digit planes of B^T (rows: 48-column tiles of 96 rows), stacked
+// with `brows` rows per plane. Real row: [Yr | -Yi]; imaginary row: [Yi | Yr].
+__global__ void slice_b_kernel(int64_t N, int64_t Np, int64_t brows, int64_t j0,
+                               const double2* __restrict__ Y, int64_t ldy, const int* __restrict__ eb,
+                               __nv_bfloat16* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = j0 + blockIdx.y;
+  if (k >= N) return;
+  const double2 y = Y[k + j * ldy];
+  const double s = ldexp(1.0, -eb[j]);
+  __nv_bfloat16 dr[OS], di[OS];
+  digits5(y.x * s, dr);
+  digits5(y.y * s, di);
+  const int64_t ld = 2 * Np;
+  const size_t plane = (size_t)brows * ld;
+  const int64_t br = brow_re(j), bi = br + 48;
+#pragma unroll
+  for (int d = 0; d < OS; ++d) {
+    __nv_bfloat16* o = out + d * plane;
+    const __nv_bfloat16 ndi = __hneg(di[d]);
+    o[br * ld + k] = dr[d];
+    o[br * ld + Np + k] = ndi;
+    o[bi * ld + k] = di[d];
+    o[bi * ld + Np + k] = dr[d];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+bool get_encoder() {
+  if (g_encode) return true;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows) {
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * Np), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * Np * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+struct Maps {
+  CUtensorMap a, b;
+};
+
+}  // namespace
+
+int64_t ozaki_np(int64_t N) { return cdiv(N, KPAD) * KPAD; }
+
+cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne) {
+  w.N = N;
+  w.ne = ne;
+  w.Np = ozaki_np(N);
+  w.brows = cdiv(ne, 48) * 96;
+  const size_t a_elems = (size_t)OS * N * 2 * w.Np;
+  const size_t b_elems = (size_t)OS * w.brows * 2 * w.Np;
+  if (!get_encoder()) return cudaErrorNotSupported;
+  cudaError_t e;
+  if ((e = cudaMalloc(&w.Ad, a_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.Bd, b_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Ad, 0, a_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Bd, 0, b_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.ea, N * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.eb, ne * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.amax, N * sizeof(unsigned long long))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.diag, N * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.err, 0, sizeof(int))) != cudaSuccess) return e;
+  Maps* maps = nullptr;
+  if ((e = cudaMallocHost(&maps, sizeof(Maps))) != cudaSuccess) return e;
+  w.maps = maps;
+  // digit planes stacked along rows: OS * N rows (A), OS * brows rows (B)
+  if (!make_map(&maps->a, w.Ad, (int64_t)OS * N, w.Np, TM) ||
+      !make_map(&maps->b, w.Bd, (int64_t)OS * w.brows, w.Np, TN))
+    return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              SMEM_BYTES);
+}
+
+void ozaki_free(OzakiWork& w) {
+  void* bufs[] = {w.Ad, w.Bd, w.ea, w.eb, w.amax, w.err, w.diag};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (w.maps) cudaFreeHost(w.maps);
+  w = OzakiWork{};
+}
+
+cudaError_t ozaki_prepare_a(cudaStream_t s, const double2* A, int64_t lda, OzakiWork& w) {
+  const int64_t N = w.N;
+  cudaError_t e = cudaMemsetAsync(w.amax, 0, N * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  rowmax_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)cdiv(N, 256), 1), 256, 0, s>>>(N, A, lda,
+                                                                                        w.amax);
+  count_launch();
+  exps_kernel<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(N, w.amax, w.ea);
+  count_launch();
+  diag_kernel<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(N, A, lda, w.diag);
+  count_launch();
+  slice_a_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(N, 32), 1), dim3(32, 8, 1), 0, s>>>(
+      N, w.Np, A, lda, w.ea, static_cast<__nv_bfloat16*>(w.Ad));
+  count_launch();
+  w.A_ready = A;
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const double2* B,
+                       int64_t ldb, const Epilogue& ep, OzakiWork& w) {
+  const int64_t N = w.N;
+  const int64_t n = ncols_end - j0;
+  if (n <= 0) return cudaSuccess;
+  // digits of the active columns of B
+  colexp_kernel<<<(unsigned)n, 256, 0, s>>>(N, j0, B, ldb, w.eb);
+  count_launch();
+  slice_b_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)n, 1), 256, 0, s>>>(
+      N, w.Np, w.brows, j0, B, ldb, w.eb, static_cast<__nv_bfloat16*>(w.Bd));
+  count_launch();
+  const Maps* maps = static_cast<const Maps*>(w.maps);
+  Params P;
+  P.N = N;
+  P.Np = w.Np;
+  P.brows = w.brows;
+  P.j0 = j0;
+  P.ncols = ncols_end;
+  P.escale_a = w.ea;
+  P.escale_b = w.eb;
+  P.diag = w.diag;
+  P.Bsrc = B;
+  P.ldbs = ldb;
+  P.mode = ep.mode;
+  P.alpha = ep.alpha;
+  P.beta = ep.beta;
+  P.gamma = ep.gamma;
+  P.X = ep.X;
+  P.ldx = ep.ldx;
+  P.Y = ep.Y;
+  P.ldy = ep.ldy;
+  P.theta = ep.theta;
+  P.partial = ep.partial;
+  P.err = w.err;
+  const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / 48 - j0 / 48 + 1), 1);
+  ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int ozaki_check(cudaStream_t s, OzakiWork& w) {
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  if (herr != 0) {
+    fprintf(stderr, "[chase] emulated-FP64 GEMM: pipeline wait expired (code %d)\n", herr);
+    cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    return CHASE_ERR_CUDA;
+  }
+  return CHASE_OK;
+}
+
+}  // namespace chase

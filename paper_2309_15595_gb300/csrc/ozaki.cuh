@@ -1,0 +1,35 @@
+// FP64-accurate complex GEMM on BF16 tensor cores (digit slicing with exact
+// chunked accumulation), see ozaki.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace chase {
+
+struct OzakiWork {
+  void* Ad = nullptr;           // 5 digit planes of [Ar | Ai], N x 2Np each (BF16)
+  void* Bd = nullptr;           // 5 digit planes of the right operand, brows x 2Np each
+  int* ea = nullptr;            // row exponents of A
+  int* eb = nullptr;            // column exponents of the right operand
+  unsigned long long* amax = nullptr;
+  double2* diag = nullptr;      // diagonal of A (applied exactly, outside the digits)
+  int* err = nullptr;
+  void* maps = nullptr;         // TMA tensor maps (pinned host)
+  const void* A_ready = nullptr;  // A whose digits are in Ad
+  int64_t N = 0, ne = 0, Np = 0, brows = 0;
+};
+
+int64_t ozaki_np(int64_t N);
+cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne);
+void ozaki_free(OzakiWork& w);
+// Digits and row exponents of A (must precede ozaki_gemm with this A).
+cudaError_t ozaki_prepare_a(cudaStream_t s, const double2* A, int64_t lda, OzakiWork& w);
+// P = A * B[:, j0:ncols_end] with the FP64 epilogue `ep` (EPI_STORE, EPI_FILTER or
+// EPI_RESID; for EPI_RESID the partials are per 32-row tile, ceil(N/32) per
+// column, indexed by absolute column). Y, X, theta, partial use absolute columns.
+cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const double2* B,
+                       int64_t ldb, const Epilogue& ep, OzakiWork& w);
+// Reads and clears the device error flag; returns a chase_status.
+int ozaki_check(cudaStream_t s, OzakiWork& w);
+
+}  // namespace chase

@@ -1,0 +1,94 @@
+"""FP64-accurate products on the BF16 tensor cores (fp64_tensor = 1) against the
+FP64 oracle.
+
+Each real operand is scaled per row/column to |x| < 1/2 (the diagonal of A is
+left out and applied exactly in FP64) and cut into five signed 8-bit digits
+(exact in BF16), leaving a truncation error below 2^-41 of the row or column
+maximum; the 15 kept digit pairs are accumulated exactly (levels 2-5) or with
+one rounding per 256-long chunk (level 6), and the dropped pairs weigh below
+2^-48. The truncation errors of the K = 2N terms of a product add with random
+signs, about sqrt(K) 2^-40 of max|a| max|y| per entry (FP64 itself: about
+sqrt(K) 2^-53). Bounds used: filter columns degs[j] * 2^-34 of the column's
+largest entry (sqrt(K) 2^-40 per degree at K <= 1400, with a factor 2 of
+margin; a lost digit level would exceed it), Ritz values 1e-12 ||A||, residual
+norms 1e-9 relative, full solves the paper's 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import chase_oracle as O
+from synth import Problem, config_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(x, lib):
+    return lib.colmajor(torch.from_numpy(np.asfortranarray(x)).cuda())
+
+
+def params(lib, p, **kw):
+    return lib.default_params(p.N, p.nev, p.nex, fp64_tensor=1, **kw)
+
+
+@pytest.mark.parametrize("N,ncols,dmax", [(512, 60, 20), (333, 37, 36), (700, 150, 36),
+                                          (130, 1, 2)])
+def test_tensor_fp64_filter_against_oracle(lib, N, ncols, dmax):
+    p = Problem(N=N, nev=ncols - ncols // 4, nex=ncols // 4, spectrum="uniform", lo=-1.0,
+                hi=4.0, reflectors=5, seed=N + 2)
+    A, V = p.matrix(), p.start_block()
+    rng = np.random.default_rng(N)
+    degs = np.sort(2 * rng.integers(1, dmax // 2 + 1, ncols)).astype(np.int32)
+    lam = p.eigenvalues()
+    b_sup = lam[-1] * 1.01
+    c, e, mu1 = (b_sup + lam[p.ne - 1]) / 2, (b_sup - lam[p.ne - 1]) / 2, lam[0]
+    ref = O.chebyshev_filter(A, V, degs, c, e, mu1)
+    with lib.Context(params(lib, p)) as ctx:
+        Vd = dev(V, lib)
+        ctx.chase_filter(dev(A, lib), Vd, ncols, degs, c, e, mu1)
+        got = Vd.cpu().numpy()
+    rel = np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    print(f"N={N} ncols={ncols}: max rel err {rel.max():.3e}")
+    assert np.all(rel <= degs * 2.0 ** -34)
+
+
+@pytest.mark.parametrize("N,n", [(400, 30), (300, 65)])
+def test_tensor_fp64_rayleigh_ritz_and_residuals(lib, N, n):
+    p = Problem(N=N, nev=n - n // 4, nex=n // 4, spectrum="uniform", lo=0.5, hi=9.0,
+                reflectors=6, seed=N + n)
+    A = p.matrix()
+    Q = np.asfortranarray(np.linalg.qr(p.start_block())[0])
+    th_o, V_o = O.rayleigh_ritz(A, Q)
+    r_o = O.residuals(A, V_o, th_o)
+    with lib.Context(params(lib, p)) as ctx:
+        Vd = dev(Q, lib)
+        Ad = dev(A, lib)
+        ritz = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.chase_rayleigh_ritz(Ad, Vd, n, ritz)
+        th = ritz.cpu().numpy()
+        resid = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.chase_residuals(Ad, Vd, ritz, n, resid)
+        r = resid.cpu().numpy()
+    assert np.abs(th - th_o).max() <= 1e-12 * p.norm2()
+    np.testing.assert_allclose(r, r_o, rtol=1e-9)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tensor_fp64_solve_c1(lib, precision):
+    p = config_problem("C1")
+    A = p.matrix()
+    V0, Q0 = p.start_block(), p.lanczos_start()
+    with lib.Context(params(lib, p, precision=precision)) as ctx:
+        Vd = dev(V0, lib)
+        ritz = torch.zeros(p.ne, dtype=torch.float64, device="cuda")
+        resid = torch.zeros_like(ritz)
+        st = ctx.chase_solve(dev(A, lib), Vd, ritz, resid, lanczos_start=dev(Q0, lib))
+    assert st["status"] == 0
+    lam = p.eigenvalues()
+    nA = p.norm2()
+    r = ritz.cpu().numpy()[:p.nev]
+    V = Vd.cpu().numpy()[:, :p.nev]
+    assert np.abs(r - lam[:p.nev]).max() <= 1e-10 * nA
+    res = np.linalg.norm(A @ V - V * r[None, :], axis=0)
+    assert res.max() <= 1e-10 * nA
+    assert np.abs(V.conj().T @ V - np.eye(p.nev)).max() <= 1e-12
