@@ -73,7 +73,7 @@ typedef struct chase_c128 { double re, im; } chase_c128;
 typedef struct chase_params {
   int64_t N;              /* matrix order, >= 2 */
   int64_t nev;            /* wanted eigenpairs, >= 1 */
-  int64_t nex;            /* extra search vectors, >= 0; nev + nex <= min(N, 7168) */
+  int64_t nex;            /* extra search vectors, >= 0; nev + nex <= min(N, 3500) */
   int32_t deg_init;       /* first-iteration filter degree (20, Section 4.2), even */
   int32_t deg_max;        /* degree cap (36, Section 4.2) */
   int32_t deg_extra;      /* safety margin added by degreeOpt (2) */

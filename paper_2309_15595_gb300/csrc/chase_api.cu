@@ -103,7 +103,8 @@ struct PhaseTimer {
 void free_ctx(chase_ctx* c) {
   if (!c) return;
   void* bufs[] = {c->V2, c->W, c->G, c->Yeig, c->gram_ws, c->dinv, c->info, c->resid_partial,
-                  c->dscal, c->perm_d, c->jw.Gw, c->jw.Gw2, c->jw.Zw, c->jw.params, c->jw.red,
+                  c->dscal, c->perm_d, c->jw.Gw, c->jw.Gw2, c->jw.Zw, c->jw.Zw2, c->jw.T,
+                  c->jw.G32a, c->jw.G32b, c->jw.Z32, c->jw.params, c->jw.red,
                   c->lw.Q, c->lw.ws, c->lw.red, c->lw.ab, c->lw.T, c->lw.theta, c->lw.Z,
                   c->lw.out4, c->lw.status};
   for (void* b : bufs)
@@ -120,9 +121,9 @@ void free_ctx(chase_ctx* c) {
 int validate_params(const chase_params* p) {
   if (!p) return CHASE_ERR_INVALID_ARG;
   if (p->N < 2 || p->nev < 1 || p->nex < 0 || p->nev + p->nex > p->N) return CHASE_ERR_INVALID_ARG;
-  // the Jacobi round kernel keeps two columns of the (nev+nex)^2 Rayleigh-Ritz
-  // matrix in shared memory: 32 (nev+nex) bytes <= 227 KB
-  if (p->nev + p->nex > 7168) return CHASE_ERR_INVALID_ARG;
+  // the Jacobi kernel keeps two FP64 columns of the (nev+nex)^2 Rayleigh-Ritz
+  // matrix and one round's rotations in shared memory: 64 (nev+nex) + 32 bytes <= 223 KB
+  if (p->nev + p->nex > 3500) return CHASE_ERR_INVALID_ARG;
   if (p->deg_init < 2 || (p->deg_init & 1) || p->deg_max < 2 || p->deg_extra < 0)
     return CHASE_ERR_INVALID_ARG;
   if (p->max_iter < 1 || !(p->tol > 0.0) || !(p->switch_tol > 0.0)) return CHASE_ERR_INVALID_ARG;
@@ -441,6 +442,11 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->jw.Gw, (size_t)ne * ne));
   A(dalloc(&c->jw.Gw2, (size_t)ne * ne));
   A(dalloc(&c->jw.Zw, (size_t)ne * ne));
+  A(dalloc(&c->jw.Zw2, (size_t)ne * ne));
+  A(dalloc(&c->jw.T, (size_t)ne * ne));
+  A(dalloc(&c->jw.G32a, (size_t)ne * ne));
+  A(dalloc(&c->jw.G32b, (size_t)ne * ne));
+  A(dalloc(&c->jw.Z32, (size_t)ne * ne));
   A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
   A(dalloc(&c->jw.red, std::max<size_t>(1024, jacobi_red_elems())));
   c->jw.nmax = ne;
@@ -462,7 +468,13 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   if (ok) A(cudaEventCreate(&c->ev0));
   if (ok) A(cudaEventCreate(&c->ev1));
   if (ok) A(cudaMemsetAsync(c->lw.status, 0, sizeof(int), c->stream));
-  if (ok) c->jw.host_red = c->host + 2 * ne + 12;
+  if (ok) {
+    c->jw.host_red = c->host + 2 * ne + 12;
+    c->jw.gram_ws = c->gram_ws;
+    c->jw.gram_ws_elems = c->gram_ws_elems;
+    c->jw.dinv = c->dinv;
+    c->jw.info = c->info;
+  }
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);

@@ -102,6 +102,15 @@ struct JacobiWork {
   double2* Gw;       // n x n working copy (ld n)
   double2* Gw2;      // second buffer: rounds alternate between Gw and Gw2
   double2* Zw;       // n x n unsorted eigenvectors (ld n)
+  double2* Zw2;      // n x n rotations of the FP64 stage
+  double2* T;        // n x n product scratch
+  float2* G32a;      // FP32 stage: two working copies and the eigenvectors
+  float2* G32b;
+  float2* Z32;
+  double2* gram_ws;  // borrowed from the context (free while Jacobi runs)
+  size_t gram_ws_elems;
+  double2* dinv;     // borrowed: POTRF diagonal-block inverses and info
+  int* info;
   double* params;    // 4 per pair
   double* red;       // reduction scratch
   double* host_red;  // pinned host scalars

@@ -17,6 +17,12 @@
 namespace chase {
 namespace {
 
+#define RC_(call)                   \
+  do {                              \
+    const int _rc = (call);         \
+    if (_rc != CHASE_OK) return _rc; \
+  } while (0)
+
 constexpr int kMaxSweeps = 40;
 constexpr int kCoopMaxGrid = 2048;  // reduction scratch holds 2 * kCoopMaxGrid partials
 
@@ -185,8 +191,84 @@ __global__ void __launch_bounds__(SJ_T)
   }
 }
 
-// ------------------------------------------------------ multi-launch version
+// ------------------------------------------------------ large-n version
+// Templated on the real type T (float or double): the large-n solver first
+// sweeps in FP32 (the FP64 pipe of this part is 1/58 of the FP32 one), then
+// re-orthonormalises the FP32 eigenvectors in FP64, forms Z^H G Z in FP64
+// (nearly diagonal) and finishes with a few FP64 sweeps.
 constexpr int LJ_T = 256;
+
+template <typename T> struct Cx;
+// eps: threshold of the rotation skip, |b| <= eps sqrt(|a d|) (unit round-off)
+template <> struct Cx<double> {
+  using C = double2;
+  static __device__ __forceinline__ C mk(double x, double y) { return make_double2(x, y); }
+  static constexpr double tiny = 1e-300, huge = 1e150, eps = 1.1102230246251565e-16;
+};
+template <> struct Cx<float> {
+  using C = float2;
+  static __device__ __forceinline__ C mk(float x, float y) { return make_float2(x, y); }
+  static constexpr float tiny = 1e-30f, huge = 1e15f, eps = 5.9604645e-8f;
+};
+
+template <typename T>
+struct RotT {
+  T c, s, px, py, app, aqq;
+};
+
+template <typename T>
+__device__ __forceinline__ RotT<T> make_rot_t(T a, T d, typename Cx<T>::C b) {
+  RotT<T> r;
+  const T ab = sqrt(b.x * b.x + b.y * b.y);
+  // threshold Jacobi: an entry below eps sqrt(|a d|) changes neither the
+  // eigenvalues nor the eigenvectors at working precision; skip it
+  if (!(ab > Cx<T>::tiny) || ab <= Cx<T>::eps * sqrt(fabs(a) * fabs(d))) {
+    r.c = T(1); r.s = T(0); r.px = T(1); r.py = T(0); r.app = a; r.aqq = d;
+    return r;
+  }
+  r.px = b.x / ab;
+  r.py = b.y / ab;
+  const T tau = (d - a) / (T(2) * ab);
+  T t;
+  if (fabs(tau) > Cx<T>::huge) t = T(0.5) / tau;
+  else t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+  r.c = T(1) / sqrt(T(1) + t * t);
+  r.s = t * r.c;
+  r.app = a - t * ab;
+  r.aqq = d + t * ab;
+  return r;
+}
+
+// (x_p, x_q) <- (x_p, x_q) J   with J = [[c, s phi], [-s conj(phi), c]]
+template <typename T, typename C>
+__device__ __forceinline__ void rot_cols_t(C& xp, C& xq, const RotT<T>& r) {
+  const T sx = r.s * r.px, sy = r.s * r.py;  // s phi
+  // xp' = c xp - conj(s phi) xq ; xq' = (s phi) xp + c xq
+  const T npx = r.c * xp.x - (sx * xq.x + sy * xq.y);
+  const T npy = r.c * xp.y - (sx * xq.y - sy * xq.x);
+  const T nqx = (sx * xp.x - sy * xp.y) + r.c * xq.x;
+  const T nqy = (sx * xp.y + sy * xp.x) + r.c * xq.y;
+  xp.x = npx; xp.y = npy; xq.x = nqx; xq.y = nqy;
+}
+// (y_p; y_q) <- J^H (y_p; y_q)
+template <typename T, typename C>
+__device__ __forceinline__ void rot_rows_t(C& yp, C& yq, const RotT<T>& r) {
+  const T sx = r.s * r.px, sy = r.s * r.py;
+  // yp' = c yp - (s phi) yq ; yq' = conj(s phi) yp + c yq
+  const T npx = r.c * yp.x - (sx * yq.x - sy * yq.y);
+  const T npy = r.c * yp.y - (sx * yq.y + sy * yq.x);
+  const T nqx = (sx * yp.x + sy * yp.y) + r.c * yq.x;
+  const T nqy = (sx * yp.y - sy * yp.x) + r.c * yq.y;
+  yp.x = npx; yp.y = npy; yq.x = nqx; yq.y = nqy;
+}
+
+template <typename T>
+__device__ __forceinline__ RotT<T> load_rot_t(const T* __restrict__ params, int k) {
+  const T* pp = params + 8 * k;
+  RotT<T> r;
+  r.c = pp[0]; r.s = pp[1]; r.px = pp[2]; r.py = pp[3]; r.app = pp[4]; r.aqq = pp[5];
+  return r;
+}
 
 __global__ void init_kernel(int64_t n, const double2* G, int64_t ldg, double2* Gw, double2* Zw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,38 +277,62 @@ __global__ void init_kernel(int64_t n, const double2* G, int64_t ldg, double2* G
   Gw[i + j * n] = G[i + j * ldg];
   Zw[i + j * n] = make_double2(i == j ? 1.0 : 0.0, 0.0);
 }
+__global__ void init32_kernel(int64_t n, const double2* G, int64_t ldg, float2* G32, float2* Z32) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n) return;
+  const double2 g = G[i + j * ldg];
+  G32[i + j * n] = make_float2((float)g.x, (float)g.y);
+  Z32[i + j * n] = make_float2(i == j ? 1.f : 0.f, 0.f);
+}
+__global__ void promote_kernel(int64_t n, const float2* Z32, double2* Z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n) return;
+  const float2 z = Z32[i + j * n];
+  Z[i + j * n] = make_double2((double)z.x, (double)z.y);
+}
+__global__ void identity_kernel(int64_t n, double2* Z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < n) Z[i + j * n] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
 
 // Pair k of round `round`, G double-buffered: the owner of pair (p, q) writes
 // the new columns p, q of J^H G J into Gnew, reading only the pre-round Gold,
 // so owners never race. Its column rotation J_k mixes columns p and q row by
-// row; then every pair's row rotation J_k'^H (each thread derives its pairs'
-// rotations from Gold itself) mixes rows (p', q') of these two columns. Z is
-// updated in place: its columns p, q belong to this owner alone.
-__device__ void process_pair(int64_t n, int m, int round, int k, const double2* __restrict__ Gold,
-                             double2* __restrict__ Gnew, double2* __restrict__ Zw, double2* colbuf) {
+// row; then every pair's row rotation J_k'^H (computed once per round, in
+// `params`) mixes rows (p', q') of these two columns. Z is updated in place:
+// its columns p, q belong to this owner alone.
+template <typename T>
+__device__ void process_pair(int64_t n, int m, int round, int k,
+                             const typename Cx<T>::C* __restrict__ Gold,
+                             typename Cx<T>::C* __restrict__ Gnew, typename Cx<T>::C* __restrict__ Zw,
+                             typename Cx<T>::C* colbuf, const T* __restrict__ params,
+                             const T* sparams) {
+  using C = typename Cx<T>::C;
   int p, q;
   rr_pair(m, round, k, p, q);
   // odd n: the pair holding the padding index n has one real column, p, which
   // still receives every other pair's row rotation
   const bool single = q >= n;
   if (single) q = p;
-  double2* gp = colbuf;
-  double2* gq = colbuf + n;
-  const Rot r = single ? make_rot(0.0, 0.0, make_double2(0.0, 0.0))
-                       : make_rot(Gold[p + (int64_t)p * n].x, Gold[q + (int64_t)q * n].x,
-                                  Gold[p + (int64_t)q * n]);
-  const double2* Gp = Gold + (int64_t)p * n;
-  const double2* Gq = Gold + (int64_t)q * n;
-  double2* Zp = Zw + (int64_t)p * n;
-  double2* Zq = Zw + (int64_t)q * n;
+  C* gp = colbuf;
+  C* gq = colbuf + n;
+  RotT<T> r = load_rot_t(params, k);
+  if (single) r.s = T(0);
+  const C* Gp = Gold + (int64_t)p * n;
+  const C* Gq = Gold + (int64_t)q * n;
+  C* Zp = Zw + (int64_t)p * n;
+  C* Zq = Zw + (int64_t)q * n;
   for (int64_t i = threadIdx.x; i < n; i += LJ_T) {
-    double2 a = Gp[i], b = Gq[i];
-    rot_cols(a, b, r);
+    C a = Gp[i], b = Gq[i];
+    if (r.s != T(0)) rot_cols_t(a, b, r);
     gp[i] = a;
     gq[i] = b;
-    if (r.s != 0.0) {
-      double2 x = Zp[i], y = Zq[i];
-      rot_cols(x, y, r);
+    if (r.s != T(0)) {
+      C x = Zp[i], y = Zq[i];
+      rot_cols_t(x, y, r);
       Zp[i] = x;
       Zq[i] = y;
     }
@@ -236,22 +342,21 @@ __device__ void process_pair(int64_t n, int m, int round, int k, const double2* 
     int pr, qr;
     rr_pair(m, round, kk, pr, qr);
     if (qr >= n) continue;
-    const Rot rk = make_rot(Gold[pr + (int64_t)pr * n].x, Gold[qr + (int64_t)qr * n].x,
-                            Gold[pr + (int64_t)qr * n]);
-    if (rk.s == 0.0) continue;
-    rot_rows(gp[pr], gp[qr], rk);
-    rot_rows(gq[pr], gq[qr], rk);
+    const RotT<T> rk = load_rot_t(sparams, kk);
+    if (rk.s == T(0)) continue;
+    rot_rows_t(gp[pr], gp[qr], rk);
+    rot_rows_t(gq[pr], gq[qr], rk);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && r.s != 0.0) {  // exact 2 x 2 block of this pair
-    gp[p] = make_double2(r.app, 0.0);
-    gq[q] = make_double2(r.aqq, 0.0);
-    gp[q] = make_double2(0.0, 0.0);
-    gq[p] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0 && r.s != T(0)) {  // exact 2 x 2 block of this pair
+    gp[p] = Cx<T>::mk(r.app, T(0));
+    gq[q] = Cx<T>::mk(r.aqq, T(0));
+    gp[q] = Cx<T>::mk(T(0), T(0));
+    gq[p] = Cx<T>::mk(T(0), T(0));
   }
   __syncthreads();
-  double2* Np_ = Gnew + (int64_t)p * n;
-  double2* Nq_ = Gnew + (int64_t)q * n;
+  C* Np_ = Gnew + (int64_t)p * n;
+  C* Nq_ = Gnew + (int64_t)q * n;
   for (int64_t i = threadIdx.x; i < n; i += LJ_T) {
     Np_[i] = gp[i];
     if (!single) Nq_[i] = gq[i];
@@ -291,7 +396,6 @@ __device__ bool grid_sync(unsigned* bar, int* status) {
           ok_s = 0;
           break;
         }
-        __nanosleep(32);
       }
     }
     __threadfence();
@@ -301,38 +405,46 @@ __device__ bool grid_sync(unsigned* bar, int* status) {
   return ok_s != 0;
 }
 
+template <typename T>
 struct CoopArgs {
   int64_t n;
   int m, max_sweeps;
-  double2* G0;
-  double2* G1;
-  double2* Z;
+  double tol_conv, tol_stag;  // converged: off <= tol_conv fro, or <= tol_stag fro and stalled
+  typename Cx<T>::C* G0;
+  typename Cx<T>::C* G1;
+  typename Cx<T>::C* Z;
+  T* params;        // 8 values per pair of the current round
   double* red;      // 2 * gridDim.x partial sums
   unsigned* bar;    // barrier counter and generation
   int* status;      // [0] error, [1] sweeps, [2] converged, [3] result in G1
 };
 
-// The whole cyclic Jacobi in one cooperative launch: per sweep a fixed-order
+// A whole cyclic Jacobi in one cooperative launch: per sweep a fixed-order
 // off-norm test (identical in every block, so the decision is uniform), then
-// the m - 1 rounds, each followed by a grid barrier.
-__global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs a) {
-  extern __shared__ double2 colbuf[];
+// the m - 1 rounds; per round the rotations are computed once (phase A) and
+// applied by the pair owners (phase B), each phase closed by a grid barrier.
+template <typename T>
+__global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs<T> a) {
+  using C = typename Cx<T>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* colbuf = reinterpret_cast<C*>(smem_raw);
+  // this round's rotations, staged once per block (8 values per pair)
+  T* sparams = reinterpret_cast<T*>(colbuf + 2 * a.n);
   __shared__ double so[LJ_T], sf[LJ_T];
   __shared__ int decide;
   const int64_t n = a.n;
   const int npairs = a.m / 2;
-  double2* Gcur = a.G0;
-  double2* Gnxt = a.G1;
+  C* Gcur = a.G0;
+  C* Gnxt = a.G1;
   double off_prev = 1e300;
   int sweep = 0;
   bool conv = false, alive = true;
   for (; sweep <= a.max_sweeps && alive; ++sweep) {
-    // off-norm and Frobenius norm of Gcur: block partials, then every block
-    // sums all partials in the same order
     double o = 0.0, f = 0.0;
     const int64_t tot = n * n;
     for (int64_t e = (int64_t)blockIdx.x * LJ_T + threadIdx.x; e < tot; e += (int64_t)gridDim.x * LJ_T) {
-      const double v = cabs2(Gcur[e]);
+      const C g = Gcur[e];
+      const double v = (double)g.x * g.x + (double)g.y * g.y;
       f += v;
       if (e % n != e / n) o += v;
     }
@@ -359,8 +471,10 @@ __global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs a) {
       }
       const double off = sqrt(to), fro = sqrt(tf);
       int d = 0;
-      if (off == 0.0 || off <= 1e-15 * fro || (off <= 1e-12 * fro && off > 0.25 * off_prev)) d = 1;
-      else if (sweep == a.max_sweeps) d = 2;
+      if (off == 0.0 || off <= a.tol_conv * fro || (off <= a.tol_stag * fro && off > 0.25 * off_prev))
+        d = 1;
+      else if (sweep == a.max_sweeps)
+        d = 2;
       off_prev = off;
       decide = d;
     }
@@ -370,10 +484,22 @@ __global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs a) {
     if (decide == 1) { conv = true; break; }
     if (decide == 2) break;
     for (int round = 0; round < a.m - 1; ++round) {
-      for (int k = blockIdx.x; k < npairs; k += gridDim.x)
-        process_pair(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf);
+      for (int k = blockIdx.x * LJ_T + threadIdx.x; k < npairs; k += gridDim.x * LJ_T) {
+        int p, q;
+        rr_pair(a.m, round, k, p, q);
+        const RotT<T> r = q < n ? make_rot_t<T>(Gcur[p + (int64_t)p * n].x, Gcur[q + (int64_t)q * n].x,
+                                                Gcur[p + (int64_t)q * n])
+                                : make_rot_t<T>(T(0), T(0), Cx<T>::mk(T(0), T(0)));
+        T* pp = a.params + 8 * k;
+        pp[0] = r.c; pp[1] = r.s; pp[2] = r.px; pp[3] = r.py; pp[4] = r.app; pp[5] = r.aqq;
+      }
       if (!grid_sync(a.bar, a.status)) { alive = false; break; }
-      double2* t = Gcur;
+      for (int e = threadIdx.x; e < 8 * npairs; e += LJ_T) sparams[e] = a.params[e];
+      __syncthreads();
+      for (int k = blockIdx.x; k < npairs; k += gridDim.x)
+        process_pair<T>(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf, a.params, sparams);
+      if (!grid_sync(a.bar, a.status)) { alive = false; break; }
+      C* t = Gcur;
       Gcur = Gnxt;
       Gnxt = t;
     }
@@ -383,6 +509,68 @@ __global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs a) {
     a.status[2] = conv ? 1 : 0;
     a.status[3] = Gcur == a.G1 ? 1 : 0;
   }
+}
+
+// Runs one cooperative Jacobi on G0 (destroyed; the result may end in G1).
+// Returns CHASE_OK and fills *sweeps, *conv, *in_g1; CHASE_ERR_CUDA on a
+// launch failure or an expired barrier.
+template <typename T>
+int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C* G1,
+             typename Cx<T>::C* Z, T* params, double* red, int max_sweeps, double tol_conv,
+             double tol_stag, int* sweeps, bool* conv, bool* in_g1) {
+  using C = typename Cx<T>::C;
+  const int m = (int)(n + (n & 1));
+  const int npairs = m / 2;
+  const size_t smem = (size_t)2 * n * sizeof(C) + (size_t)8 * npairs * sizeof(T);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<T>, LJ_T, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return CHASE_ERR_CUDA;
+  // one pair per block where the blocks fit, so pairs run concurrently
+  const int grid = std::min(std::min(npairs, per_sm * nsm), kCoopMaxGrid);
+  unsigned* bar = reinterpret_cast<unsigned*>(red + 2 * kCoopMaxGrid);
+  int* st = reinterpret_cast<int*>(red + 2 * kCoopMaxGrid + 2);
+  if (cudaMemsetAsync(red + 2 * kCoopMaxGrid, 0, 8 * sizeof(double), s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  CoopArgs<T> args;
+  args.n = n;
+  args.m = m;
+  args.max_sweeps = max_sweeps;
+  args.tol_conv = tol_conv;
+  args.tol_stag = tol_stag;
+  args.G0 = G0;
+  args.G1 = G1;
+  args.Z = Z;
+  args.params = params;
+  args.red = red;
+  args.bar = bar;
+  args.status = st;
+  void* kargs[] = {&args};
+  if (cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel<T>, dim3(grid), dim3(LJ_T), kargs,
+                                  smem, s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  count_launch();
+  int hst[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CHASE_ERR_CUDA;
+  if (hst[0] != 0) {
+    fprintf(stderr, "[chase] Jacobi: grid barrier wait expired\n");
+    return CHASE_ERR_CUDA;
+  }
+  *sweeps = hst[1];
+  *conv = hst[2] != 0;
+  *in_g1 = hst[3] != 0;
+  return CHASE_OK;
 }
 
 __global__ void rank_kernel(int64_t n, const double2* Gw, double* w, int* rank) {
@@ -450,59 +638,59 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     if (sweeps_out) *sweeps_out = 0;
     return hs ? CHASE_ERR_HEEV_NOCONV : CHASE_OK;
   }
-  const int m = (int)(n + (n & 1));
-  const int npairs = m / 2;
-  const size_t smem = (size_t)2 * n * sizeof(double2);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return CHASE_ERR_CUDA;
-  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, LJ_T, smem) !=
+  // --- FP32 sweeps on the converted matrix
+  const dim3 g2((unsigned)cdiv(n, 128), (unsigned)n, 1);
+  init32_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.G32a, wk.Z32); count_launch();
+  int sw32 = 0, sw64 = 0;
+  bool conv32 = false, conv = false, in_g1 = false;
+  RC_(run_coop<float>(s, n, wk.G32a, wk.G32b, wk.Z32, reinterpret_cast<float*>(wk.params), wk.red,
+                      30, 4e-6, 1e-4, &sw32, &conv32, &in_g1));
+  // --- FP64: Z = orthonormalised FP32 eigenvectors, G' = Z^H G Z
+  promote_kernel<<<g2, 128, 0, s>>>(n, wk.Z32, wk.Zw); count_launch();
+  if (zgram(s, n, n, n, wk.Zw, n, wk.Zw, n, wk.T, n, true, wk.gram_ws, wk.gram_ws_elems) !=
           cudaSuccess ||
-      per_sm < 1)
+      potrf_upper(s, n, wk.T, n, wk.dinv, wk.info) != cudaSuccess ||
+      trsm_right_upper(s, n, n, wk.Zw, n, wk.T, n, wk.dinv, wk.info) != cudaSuccess)
     return CHASE_ERR_CUDA;
-  const int grid = std::min(std::min(npairs, per_sm * nsm), kCoopMaxGrid);
-  double2* Gcur = wk.Gw;
-  init_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, G, ldg, Gcur, wk.Zw); count_launch();
-  // barrier words and status live in the reduction scratch after the partials
-  unsigned* bar = reinterpret_cast<unsigned*>(wk.red + 2 * kCoopMaxGrid);
-  int* st = reinterpret_cast<int*>(wk.red + 2 * kCoopMaxGrid + 2);
-  if (cudaMemsetAsync(wk.red + 2 * kCoopMaxGrid, 0, 8 * sizeof(double), s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
-  CoopArgs args;
-  args.n = n;
-  args.m = m;
-  args.max_sweeps = kMaxSweeps;
-  args.G0 = wk.Gw;
-  args.G1 = wk.Gw2;
-  args.Z = wk.Zw;
-  args.red = wk.red;
-  args.bar = bar;
-  args.status = st;
-  void* kargs[] = {&args};
-  if (cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(LJ_T), kargs,
-                                  smem, s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
-  count_launch();
-  int hst[4] = {0, 0, 0, 0};
-  if (cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  int hinfo = 0;
+  if (cudaMemcpyAsync(&hinfo, wk.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return CHASE_ERR_CUDA;
-  if (hst[0] != 0) {
-    fprintf(stderr, "[chase] Jacobi: grid barrier wait expired\n");
-    return CHASE_ERR_CUDA;
+  double2* Gcur = wk.Gw;
+  if (hinfo != 0) {
+    // the FP32 basis is unusable (should not happen): plain FP64 Jacobi from G
+    init_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.Gw, wk.Zw); count_launch();
+  } else {
+    Epilogue ep{};
+    ep.mode = EPI_STORE;
+    ep.Y = wk.T;
+    ep.ldy = n;
+    if (zgemm_nn(s, n, n, n, G, ldg, wk.Zw, n, ep) != cudaSuccess ||                  // T = G Z
+        zgram(s, n, n, n, wk.Zw, n, wk.T, n, wk.Gw, n, false, wk.gram_ws, wk.gram_ws_elems) !=
+            cudaSuccess ||                                                            // Z^H G Z
+        hermitian_part(s, n, wk.Gw, n) != cudaSuccess)
+      return CHASE_ERR_CUDA;
   }
-  if (hst[3]) Gcur = wk.Gw2;
-  const int sweep = hst[1];
-  const bool conv = hst[2] != 0;
+  double2* Zrot = hinfo != 0 ? wk.Zw : wk.Zw2;
+  if (hinfo == 0) {
+    identity_kernel<<<g2, 128, 0, s>>>(n, wk.Zw2); count_launch();
+  }
+  RC_(run_coop<double>(s, n, wk.Gw, wk.Gw2, Zrot, wk.params, wk.red, kMaxSweeps, 1e-15, 1e-12,
+                       &sw64, &conv, &in_g1));
+  if (in_g1) Gcur = wk.Gw2;
+  double2* Zfinal = Zrot;
+  if (hinfo == 0) {  // eigenvectors of G: Z (FP32 stage) times the FP64 rotations
+    Epilogue ep{};
+    ep.mode = EPI_STORE;
+    ep.Y = wk.T;
+    ep.ldy = n;
+    if (zgemm_nn(s, n, n, n, wk.Zw, n, wk.Zw2, n, ep) != cudaSuccess) return CHASE_ERR_CUDA;
+    Zfinal = wk.T;
+  }
+  const int sweep = sw32 + sw64;
   int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
   rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, Gcur, w, rank); count_launch();
-  permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, wk.Zw, rank,
+  permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, Zfinal, rank,
                                                                                     Z, ldz); count_launch();
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   if (sweeps_out) *sweeps_out = sweep;
