@@ -61,6 +61,8 @@ def parse():
                     help="comma list of modes (fp64, fp64t, mixed, mixedt) for full solves to "
                          "resid <= tol instead of the per-iteration step")
     ap.add_argument("--max-iter", type=int, default=100)
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the tensor-core FP64 variant measured beside the DFMA line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -391,6 +393,41 @@ def run_gpu(args):
                                     "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": desc + f" (measured {meas:.1f} s)"}
     ctx.close()
+    if prec == lib.CHASE_FP64 and not args.fp64_tensor and not args.no_variant:
+        # the same step with the FP64 N x N products on the tensor cores
+        # (exact BF16 digit slicing), timed under the same rules
+        vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec, fp64_tensor=1)
+        vctx = lib.Context(vprm, stream)
+
+        def vstep():
+            V.copy_(V0d)
+            return vctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+
+        for _ in range(args.warmup):
+            vstep()
+        torch.cuda.synchronize()
+        barrier()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        vstats = [vstep() for _ in range(args.steps)]
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vvalue, vms, _ = aggregate_over_ranks(v0.elapsed_time(v1), args.steps, dist, dev)
+        vctx.close()
+        vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
+        vach = flops_launch / (vfilter / deg / 1000.0) / 1e12
+        peak = measured_bf16_peak()
+        line["variant_fp64_tensor"] = {
+            "value": vvalue, "unit": "ChASE iterations/s", "ms_per_step": vms / args.steps,
+            "dtype": "f64 (bf16 digit slices, exact accumulation; ~2^-40 relative per product)",
+            "roofline": {"kernel": "ozaki_gemm_kernel<EPI_FILTER>", "bound": "tensor",
+                         "achieved": 15.0 * vach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": 15.0 * vach / peak, "fp64_equivalent_tflops": vach,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"},
+            "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in
+                         ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid",
+                          "ms_total")},
+            "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
