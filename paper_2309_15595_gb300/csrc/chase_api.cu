@@ -335,9 +335,28 @@ int resid_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* V, in
   return CHASE_OK;
 }
 
+// Lanczos block product on the tensor cores (digits of A prepared by the caller).
+cudaError_t lanczos_tensor_matmul(void* vc, const double2* Q, int64_t ldq, int nvec, double2* W,
+                                  int64_t ldw) {
+  chase_ctx* c = static_cast<chase_ctx*>(vc);
+  Epilogue ep{};
+  ep.mode = EPI_STORE;
+  ep.Y = W;
+  ep.ldy = ldw;
+  return ozaki_gemm(c->stream, nvec, 0, Q, ldq, ep, c->ow);
+}
+
 int lanczos_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q0, int64_t ldq,
                  int nvec, double* out4_h) {
+  if (c->p.fp64_tensor) {
+    RC(prepare_a(c, A, lda));
+    c->lw.matmul = lanczos_tensor_matmul;
+    c->lw.matmul_ctx = c;
+  } else {
+    c->lw.matmul = nullptr;
+  }
   CK(lanczos_bounds(c->stream, c->N, A, lda, Q0, ldq, nvec, c->p.lanczos_steps, c->ne, c->lw));
+  if (c->p.fp64_tensor) RC(ozaki_check(c->stream, c->ow));
   CK(cudaMemcpyAsync(out4_h, c->lw.out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   int st = 0;
   CK(cudaMemcpyAsync(&st, c->lw.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -562,6 +581,15 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   CK(cudaEventRecord(t_start, c->stream));
   const long long launches0 = launch_count();
 
+  if (P.fp64_tensor) {  // digits of A once for every tensor-core FP64 product of this solve
+    c->oz_a_valid = false;
+    RC(prepare_a(c, A, lda));
+    c->oz_a_valid = true;
+  }
+  struct ResetDigits {
+    chase_ctx* c;
+    ~ResetDigits() { c->oz_a_valid = false; }
+  } reset_digits{c};
   double b4[4];
   {
     PhaseTimer tm(c, &st.ms_lanczos);
@@ -577,15 +605,6 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   st.mu_ne = mu_ne;
   st.norm_est = norm_est;
   const double tol_abs = P.tol * norm_est;
-  if (P.fp64_tensor) {  // digits of A once for every tensor-core FP64 product of this solve
-    c->oz_a_valid = false;
-    RC(prepare_a(c, A, lda));
-    c->oz_a_valid = true;
-  }
-  struct ResetDigits {
-    chase_ctx* c;
-    ~ResetDigits() { c->oz_a_valid = false; }
-  } reset_digits{c};
 
   std::vector<int32_t> degs(ne, P.deg_init);
   std::vector<double> rz(ne, 0.0), rs(ne, 0.0);

@@ -144,6 +144,11 @@ struct LanczosWork {
   double2* Z;        // batch x k x k
   double* out4;      // b_sup, mu_1, mu_ne, norm_est
   int* status;
+  // optional replacement of the block product W = A Q (e.g. on the tensor
+  // cores); nullptr: the FP64 skinny GEMM
+  cudaError_t (*matmul)(void* ctx, const double2* Q, int64_t ldq, int nvec, double2* W,
+                        int64_t ldw) = nullptr;
+  void* matmul_ctx = nullptr;
 };
 cudaError_t lanczos_bounds(cudaStream_t s, int64_t N, const double2* A, int64_t lda,
                            const double2* Q0, int64_t ldq, int nvec, int k, int64_t ne,

@@ -9,24 +9,25 @@
 // FP64 in the epilogue (A_ii B_ij): the row scales then follow the off-diagonal
 // entries, which keeps their relative precision when A is diagonally dominant.
 // Row i of the left operand is scaled by 2^-e_i and column j of the right one
-// by 2^-f_j so every entry x has |x| < 1/2, then cut into S = 5 signed 8-bit
-// digits, x = sum_s d_s 2^-8s + O(2^-40), |d_s| <= 128, computed exactly in
-// FP64; every digit is exact in BF16. The product keeps the 15 digit pairs
-// (s, t) with s + t <= 6; pair (s, t) contributes at weight 2^-8(s+t).
+// by 2^-f_j so every entry x has |x| < 1/2, then cut into S = 6 signed 8-bit
+// digits, x = sum_s d_s 2^-8s + O(2^-48), |d_s| <= 128, computed exactly in
+// FP64; every digit is exact in BF16. The product keeps the 21 digit pairs
+// (s, t) with s + t <= 7; pair (s, t) contributes at weight 2^-8(s+t).
 // Digit products are < 2^14 and exact; the FP32 tensor-memory accumulator of
 // one level L = s + t stays an exact integer over a chunk of 256 K values
 // (at most (L-1) 2^22 <= 2^24 for L <= 5), so after every chunk the epilogue
 // warps move levels 2-5 into exact int64 accumulators (shifted into one common
-// scale, at most 2^55 in total) and add level 6, whose weight is 2^-8 below
-// that scale, rounded to it (error <= 1/2 unit of 2^-40 per chunk).
-// The result is W = 2^(e_i + f_j) acc 2^-40, accurate to a few units of 2^-40
-// relative to |A_i.| |Y_.j| per term: FP64-class.
+// scale, at most 2^54 in total) and levels 6-7, whose weights are at most
+// 2^-32 of the leading level, into an FP32 accumulator (its rounding is then
+// below 2^-56 of the leading level).
+// The result is W = 2^(e_i + f_j) (acc 2^-40 + acc67 2^-48), accurate to a few
+// units of 2^-48 relative to |A_i.| |Y_.j| per term: FP64-class.
 //
-// Kernel structure (128 x 96 real output tile = 48 complex columns, 10 warps):
-//   warp 0    TMA producer: 5 A digit tiles (128 x 32) and 5 B digit tiles
-//             (96 x 32) per K block into a 3-stage ring (64B swizzle)
-//   warp 1    TMEM allocator and MMA issuer: 15 tcgen05.mma (M=128, N=96,
-//             K=16) per 16-wide K step, one accumulator per level (5 x 96
+// Kernel structure (128 x 64 real output tile = 32 complex columns, 10 warps):
+//   warp 0    TMA producer: 6 A digit tiles (128 x 32) and 6 B digit tiles
+//             (64 x 32) per K block into a 3-stage ring (64B swizzle)
+//   warp 1    TMEM allocator and MMA issuer: 21 tcgen05.mma (M=128, N=64,
+//             K=16) per 16-wide K step, one accumulator per level (6 x 64
 //             TMEM columns); after each 256-wide chunk it hands the
 //             accumulators to the epilogue and waits until they are drained
 //   warps 2-9 epilogue: warp w owns TMEM lane quarter w % 4 and half of the
@@ -43,17 +44,18 @@
 namespace chase {
 namespace {
 
-constexpr int OS = 5;                    // digits per operand
-constexpr int TM = 128, TN = 96, TK = 32, STAGES = 3;
+constexpr int OS = 6;                    // digits per operand
+constexpr int TM = 128, TN = 64, TK = 32, STAGES = 3;
 constexpr int CHUNK_KB = 8;              // K blocks per exact chunk (256 values)
 constexpr int A_TILE = TM * TK * 2;      // 8 KB per digit
-constexpr int B_TILE = TN * TK * 2;      // 6 KB per digit
-constexpr int STAGE_BYTES = OS * (A_TILE + B_TILE);  // 70 KB
+constexpr int B_TILE = TN * TK * 2;      // 4 KB per digit
+constexpr int STAGE_BYTES = OS * (A_TILE + B_TILE);  // 72 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int KPAD = 128;                // K-half padding: 2 Np is a multiple of 256
-constexpr int HC = TN / 4;               // complex columns per epilogue warp half (24)
+constexpr int HC = TN / 4;               // complex columns per epilogue warp half (16)
+constexpr int CT = TN / 2;               // complex columns per tile (32)
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
 
 // ------------------------------------------------------------ PTX helpers
@@ -130,7 +132,7 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
-// 16 and 8 consecutive TMEM columns of this warp's 32 lanes.
+// 16 consecutive TMEM columns of this warp's 32 lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -143,23 +145,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// B^T row of complex column j: tiles of 48 complex columns, 96 rows each,
+// B^T row of complex column j: tiles of CT complex columns, TN rows each,
 // real parts first.
-__device__ __forceinline__ int64_t brow_re(int64_t j) { return (j / 48) * 96 + (j % 48); }
+__device__ __forceinline__ int64_t brow_re(int64_t j) { return (j / CT) * TN + (j % CT); }
 
 struct Params {
   int64_t N, Np, j0, ncols;   // rows, padded K half, first active column, end column
@@ -193,7 +185,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * TM;
-  const int64_t tile = P.j0 / 48 + blockIdx.y;    // absolute 48-column tile
+  const int64_t tile = P.j0 / CT + blockIdx.y;    // absolute CT-column tile
   const int nkb = (int)((2 * P.Np) / TK);
   const int nchunks = nkb / CHUNK_KB;
 
@@ -298,9 +290,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int h = (warp - 2) >> 2;            // complex column half: [h*24, h*24+24)
     const int64_t row = m0 + q * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-    long long acc[2 * HC];                    // re[0..24), im[24..48), weight 2^-40
+    long long acc[2 * HC];                    // re[0..16), im[16..32): levels 2-5, weight 2^-40
+    float acc67[2 * HC];                      // levels 6-7, weight 2^-48
 #pragma unroll
-    for (int j = 0; j < 2 * HC; ++j) acc[j] = 0;
+    for (int j = 0; j < 2 * HC; ++j) {
+      acc[j] = 0;
+      acc67[j] = 0.f;
+    }
     bool go = true;
     for (int c = 0; c < nchunks; ++c) {
       const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), (uint32_t)c & 1u, P.err, 15);
@@ -308,26 +304,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!go) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // levels 2..5 are exact integers below 2^24 per chunk: int64 at weight
-      // 2^-40 (level L shifted by 8 (5 - L) bits); level 6 (weight 2^-48) is
-      // rounded to that weight once per chunk (error <= 1/2 unit of 2^-40)
+      // 2^-40 (level L shifted by 8 (5 - L) bits); levels 6 and 7 (weights
+      // 2^-48, 2^-56, at most 2^-24 of the leading level) in FP32
 #pragma unroll
       for (int L = 2; L <= OS + 1; ++L) {
 #pragma unroll
         for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
           float v[HC];
-          const uint32_t base = tl + (uint32_t)((L - 2) * TN + part * 48 + h * HC);
+          const uint32_t base = tl + (uint32_t)((L - 2) * TN + part * CT + h * HC);
           tmem_ld16(base, v);
-          tmem_ld8(base + 16, v + 16);
           tmem_wait_ld();
-          if (L <= OS) {
-            const int sh = 8 * (OS - L);
+          if (L <= 5) {
+            const int sh = 8 * (5 - L);
 #pragma unroll
             for (int j = 0; j < HC; ++j)
               acc[part * HC + j] += (long long)__float2int_rn(v[j]) << sh;
           } else {
+            const float w = L == 6 ? 1.0f : 0.00390625f;
 #pragma unroll
-            for (int j = 0; j < HC; ++j)
-              acc[part * HC + j] += (long long)__float2int_rn(v[j] * 0.00390625f);
+            for (int j = 0; j < HC; ++j) acc67[part * HC + j] = fmaf(w, v[j], acc67[part * HC + j]);
           }
         }
       }
@@ -342,13 +337,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const double2 dg = P.diag[row];
 #pragma unroll
       for (int jj = 0; jj < HC; ++jj) {
-        const int64_t col = tile * 48 + h * HC + jj;
+        const int64_t col = tile * CT + h * HC + jj;
         rsq[jj] = 0.0;
         if (col < P.j0 || col >= P.ncols) continue;
         const double sc = sa * ldexp(1.0, P.escale_b[col]);
         const double2 b = P.Bsrc[row + col * P.ldbs];
-        const double wr = fma(dg.x, b.x, fma(-dg.y, b.y, sc * ((double)acc[jj] * 0x1p-40)));
-        const double wi = fma(dg.x, b.y, fma(dg.y, b.x, sc * ((double)acc[HC + jj] * 0x1p-40)));
+        const double lr = fma((double)acc[jj], 0x1p-40, (double)acc67[jj] * 0x1p-48);
+        const double li = fma((double)acc[HC + jj], 0x1p-40, (double)acc67[HC + jj] * 0x1p-48);
+        const double wr = fma(dg.x, b.x, fma(-dg.y, b.y, sc * lr));
+        const double wi = fma(dg.x, b.y, fma(dg.y, b.x, sc * li));
         if (P.mode == EPI_STORE) {
           P.Y[row + col * P.ldy] = make_double2(wr, wi);
         } else if (P.mode == EPI_FILTER) {
@@ -382,7 +379,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         double v = rsq[jj];
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        const int64_t col = tile * 48 + h * HC + jj;
+        const int64_t col = tile * CT + h * HC + jj;
         if (lane == 0 && t32 < nt32 && col >= P.j0 && col < P.ncols) P.partial[t32 + col * nt32] = v;
       }
     }
@@ -398,7 +395,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------------ digit prep
-__device__ __forceinline__ void digits5(double x, __nv_bfloat16* d) {
+__device__ __forceinline__ void digits_of(double x, __nv_bfloat16* d) {
   // |x| < 1/2: x = sum_s d_s 2^-8s + r, |d_s| <= 128 (exact in FP64 and BF16)
 #pragma unroll
   for (int s = 0; s < OS; ++s) {
@@ -443,7 +440,7 @@ __global__ void exps_kernel(int64_t n, const unsigned long long* __restrict__ mx
   if (i < n) e[i] = scale_exp(__longlong_as_double((long long)mx[i]));
 }
 
-// A -> 5 digit planes, each N rows x 2 Np (row-major [Ar | Ai]), stacked.
+// A -> OS digit planes, each N rows x 2 Np (row-major [Ar | Ai]), stacked.
 __global__ void slice_a_kernel(int64_t N, int64_t Np, const double2* __restrict__ A, int64_t lda,
                                const int* __restrict__ ea, __nv_bfloat16* __restrict__ out) {
   __shared__ double2 tile[32][33];
@@ -462,8 +459,8 @@ __global__ void slice_a_kernel(int64_t N, int64_t Np, const double2* __restrict_
       const double2 a = i == k ? make_double2(0.0, 0.0) : tile[tx][r];
       const double s = ldexp(1.0, -ea[i]);
       __nv_bfloat16 dr[OS], di[OS];
-      digits5(a.x * s, dr);
-      digits5(a.y * s, di);
+      digits_of(a.x * s, dr);
+      digits_of(a.y * s, di);
 #pragma unroll
       for (int d = 0; d < OS; ++d) {
         out[d * plane + i * ld + k] = dr[d];
@@ -492,7 +489,7 @@ __global__ void colexp_kernel(int64_t N, int64_t j0, const double2* __restrict__
   if (threadIdx.x == 0) eb[j] = scale_exp(red[0]);
 }
 
-// Y columns -> 5 digit planes of B^T (rows: 48-column tiles of 96 rows), stacked
+// Y columns -> OS digit planes of B^T (rows: 32-column tiles of 64 rows), stacked
 // with `brows` rows per plane. Real row: [Yr | -Yi]; imaginary row: [Yi | Yr].
 __global__ void slice_b_kernel(int64_t N, int64_t Np, int64_t brows, int64_t j0,
                                const double2* __restrict__ Y, int64_t ldy, const int* __restrict__ eb,
@@ -503,11 +500,11 @@ __global__ void slice_b_kernel(int64_t N, int64_t Np, int64_t brows, int64_t j0,
   const double2 y = Y[k + j * ldy];
   const double s = ldexp(1.0, -eb[j]);
   __nv_bfloat16 dr[OS], di[OS];
-  digits5(y.x * s, dr);
-  digits5(y.y * s, di);
+  digits_of(y.x * s, dr);
+  digits_of(y.y * s, di);
   const int64_t ld = 2 * Np;
   const size_t plane = (size_t)brows * ld;
-  const int64_t br = brow_re(j), bi = br + 48;
+  const int64_t br = brow_re(j), bi = br + CT;
 #pragma unroll
   for (int d = 0; d < OS; ++d) {
     __nv_bfloat16* o = out + d * plane;
@@ -554,7 +551,7 @@ cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne) {
   w.N = N;
   w.ne = ne;
   w.Np = ozaki_np(N);
-  w.brows = cdiv(ne, 48) * 96;
+  w.brows = cdiv(ne, CT) * TN;
   const size_t a_elems = (size_t)OS * N * 2 * w.Np;
   const size_t b_elems = (size_t)OS * w.brows * 2 * w.Np;
   if (!get_encoder()) return cudaErrorNotSupported;
@@ -640,7 +637,7 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
   P.theta = ep.theta;
   P.partial = ep.partial;
   P.err = w.err;
-  const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / 48 - j0 / 48 + 1), 1);
+  const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / CT - j0 / CT + 1), 1);
   ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
   count_launch();
   return cudaGetLastError();

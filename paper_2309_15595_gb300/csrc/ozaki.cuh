@@ -7,8 +7,8 @@
 namespace chase {
 
 struct OzakiWork {
-  void* Ad = nullptr;           // 5 digit planes of [Ar | Ai], N x 2Np each (BF16)
-  void* Bd = nullptr;           // 5 digit planes of the right operand, brows x 2Np each
+  void* Ad = nullptr;           // 6 digit planes of [Ar | Ai], N x 2Np each (BF16)
+  void* Bd = nullptr;           // 6 digit planes of the right operand, brows x 2Np each
   int* ea = nullptr;            // row exponents of A
   int* eb = nullptr;            // column exponents of the right operand
   unsigned long long* amax = nullptr;

@@ -195,7 +195,8 @@ cudaError_t lanczos_bounds(cudaStream_t s, int64_t N, const double2* A, int64_t 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int j = 0; j < k; ++j) {
-    e = zgemm_skinny(s, N, nvec, A, lda, Q, N, W, N, w.ws);  // W = A q
+    e = w.matmul ? w.matmul(w.matmul_ctx, Q, N, nvec, W, N)   // W = A q
+                 : zgemm_skinny(s, N, nvec, A, lda, Q, N, W, N, w.ws);
     if (e != cudaSuccess) return e;
     // W -= beta_{j-1} q_prev ; alpha_j = Re(q^H W)
     lz_partial_kernel<<<gp, VT, 0, s>>>(1, N, nvec, nullptr, 0, Q, Qp, W, w.ab, j, kmax, w.red); count_launch();
