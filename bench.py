@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-solution at resid≤1e-10, mixed vs FP64; filter TFLOP/s vs peak"
 # FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz (max SM clock)
+# six signed 8-bit digits per real operand; the products of digit pairs s + t <= 7
+# are issued (1 + 2 + ... + 6 = 21 BF16 MMAs per real multiply-add)
+OZ_PAIRS = 21.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
@@ -52,7 +55,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="C2")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--fp64-tensor", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--fp64-tensor", type=int, default=1, choices=[0, 1],
                     help="1: FP64 N x N products on the tensor cores (exact digit slicing)")
     ap.add_argument("--N", type=int, default=0, help="override the workload's order (profiling)")
     ap.add_argument("--nev", type=int, default=0)
@@ -62,7 +65,16 @@ def parse():
                          "resid <= tol instead of the per-iteration step")
     ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--no-variant", action="store_true",
-                    help="skip the tensor-core FP64 variant measured beside the DFMA line")
+                    help="skip the other precision modes measured beside the headline")
+    ap.add_argument("--grad", action="store_true",
+                    help="differentiation workload (C4): gradient timing and checks")
+    ap.add_argument("--grad-fd", type=int, default=2,
+                    help="finite-difference directions checked in --grad mode")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched warm-start sequence (C5)")
+    ap.add_argument("--batch-problems", type=int, default=96)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-threads", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -239,6 +251,46 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU
+def filter_roofline(lib, prec, tensor, ms_filter, N, ne, deg):
+    """Roofline of the dominant kernel (the filter product, deg launches per
+    step at iteration 1 with all ne vectors active): per-launch time from the
+    library's CUDA events on the launching stream over the timed steps."""
+    launch_ms = ms_filter / deg
+    flops_launch = 8.0 * N * N * ne
+    achieved = flops_launch / (launch_ms / 1000.0) / 1e12
+    if prec == lib.CHASE_FP64 and tensor:
+        # issued tensor work: OZ_PAIRS BF16 digit-pair products per real MAC of the planar GEMM
+        peak = measured_bf16_peak()
+        return {"kernel": "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)",
+                "bound": "tensor", "achieved": OZ_PAIRS * achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": OZ_PAIRS * achieved / peak, "traffic": None,
+                "launches_per_step": deg, "flops_per_launch": OZ_PAIRS * flops_launch,
+                "fp64_equivalent_tflops": achieved,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    if prec == lib.CHASE_FP64:
+        return {"kernel": "zgemm_kernel<EPI_FILTER> (filter HEMM, Eq. 1)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "launches_per_step": deg, "flops_per_launch": flops_launch,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz"}
+    # issued tensor work: three BF16 products per real MAC of the planar GEMM
+    peak = measured_bf16_peak()
+    return {"kernel": "mixed_filter_kernel (tcgen05 split-BF16x3 filter HEMM)",
+            "bound": "tensor", "achieved": 3.0 * achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": 3.0 * achieved / peak, "traffic": None, "launches_per_step": deg,
+            "flops_per_launch": 3.0 * flops_launch, "fp64_equivalent_tflops": achieved,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+
+
+PHASES = ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid", "ms_total")
+
+
+def dtype_name(lib, prec, tensor):
+    if prec == lib.CHASE_FP64:
+        return "f64 (bf16 digit slices, exact accumulation)" if tensor else "f64"
+    return "bf16x3+f64"
+
+
 def run_gpu(args):
     import torch
 
@@ -270,65 +322,41 @@ def run_gpu(args):
     ritz = torch.zeros(ne, dtype=torch.float64, device=dev)
     resid = torch.zeros_like(ritz)
     stream = torch.cuda.current_stream(dev)
-    ctx = lib.Context(params, stream)
-
-    def step():
-        V.copy_(V0d)
-        return ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier()
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    stats = [step() for _ in range(args.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    value, ms, world = aggregate_over_ranks(ev0.elapsed_time(ev1), args.steps, dist, dev)
-    ms_per_step = ms / args.steps
+    def timed(prm, warmup, steps, clocks=None):
+        """warmup untimed steps, then `steps` steps between CUDA events on the
+        launching stream (barrier + synchronize on both sides)"""
+        cx = lib.Context(prm, stream)
 
-    # dominant kernel: the filter GEMM (deg launches per iteration at iteration 1,
-    # all ne vectors active); per-launch time from the library's CUDA events on
-    # the launching stream over the timed steps
+        def step():
+            V.copy_(V0d)
+            return cx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        if clocks:
+            clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        stats = [step() for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        value, ms, _ = aggregate_over_ranks(ev0.elapsed_time(ev1), steps, dist, dev)
+        return cx, stats, value, ms / steps, clk
+
+    ctx, stats, value, ms_per_step, clk = timed(params, args.warmup, args.steps,
+                                                ClockSampler(dev.index))
     ms_filter = sum(s["ms_filter"] for s in stats) / len(stats)
-    launch_ms = ms_filter / deg
-    flops_launch = 8.0 * N * N * ne
-    achieved = flops_launch / (launch_ms / 1000.0) / 1e12
-    if prec == lib.CHASE_FP64 and args.fp64_tensor:
-        # issued tensor work: 15 BF16 digit-pair products per real MAC of the planar GEMM
-        issued = 15.0 * flops_launch / (launch_ms / 1000.0) / 1e12
-        peak = measured_bf16_peak()
-        roof = {"kernel": "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)",
-                "bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
-                "frac": issued / peak, "traffic": None, "launches_per_step": deg,
-                "flops_per_launch": 15.0 * flops_launch, "fp64_equivalent_tflops": achieved,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-    elif prec == lib.CHASE_FP64:
-        roof = {"kernel": "zgemm_kernel<EPI_FILTER> (filter HEMM, Eq. 1)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "launches_per_step": deg, "flops_per_launch": flops_launch,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz"}
-    else:
-        # issued tensor work: three BF16 products per real MAC of the planar GEMM
-        issued = 3.0 * flops_launch / (launch_ms / 1000.0) / 1e12
-        peak = measured_bf16_peak()
-        roof = {"kernel": "mixed_filter_kernel (tcgen05 split-BF16x3 filter HEMM)",
-                "bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
-                "frac": issued / peak, "traffic": None, "launches_per_step": deg,
-                "flops_per_launch": 3.0 * flops_launch,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-    phases = {k: sum(s[k] for s in stats) / len(stats) for k in
-              ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid", "ms_total")}
+    roof = filter_roofline(lib, prec, args.fp64_tensor, ms_filter, N, ne, deg)
+    phases = {k: sum(s[k] for s in stats) / len(stats) for k in PHASES}
     phases["heev_sweeps"] = stats[-1]["heev_sweeps"]
     launches = int(sum(s["kernel_launches"] for s in stats))
 
@@ -336,8 +364,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "ChASE iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f64 (bf16 digit slices, exact accumulation)" if args.fp64_tensor else "f64")
-                 if prec == lib.CHASE_FP64 else "bf16x3+f64", "data": "synthetic",
+        "dtype": dtype_name(lib, prec, args.fp64_tensor), "data": "synthetic",
         "config": {"workload": f"{name}: " + workload_desc(p, deg), "N": N, "nev": p.nev,
                    "nex": p.nex, "deg": deg, "precision": args.precision,
                    "fp64_tensor": args.fp64_tensor,
@@ -392,42 +419,33 @@ def run_gpu(args):
             line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "ChASE iterations/s",
                                     "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": desc + f" (measured {meas:.1f} s)"}
+        del A_h
     ctx.close()
-    if prec == lib.CHASE_FP64 and not args.fp64_tensor and not args.no_variant:
-        # the same step with the FP64 N x N products on the tensor cores
-        # (exact BF16 digit slicing), timed under the same rules
-        vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=prec, fp64_tensor=1)
-        vctx = lib.Context(vprm, stream)
 
-        def vstep():
-            V.copy_(V0d)
-            return vctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
-
-        for _ in range(args.warmup):
-            vstep()
-        torch.cuda.synchronize()
-        barrier()
-        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        v0.record(stream)
-        vstats = [vstep() for _ in range(args.steps)]
-        v1.record(stream)
-        torch.cuda.synchronize()
-        vvalue, vms, _ = aggregate_over_ranks(v0.elapsed_time(v1), args.steps, dist, dev)
-        vctx.close()
-        vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
-        vach = flops_launch / (vfilter / deg / 1000.0) / 1e12
-        peak = measured_bf16_peak()
-        line["variant_fp64_tensor"] = {
-            "value": vvalue, "unit": "ChASE iterations/s", "ms_per_step": vms / args.steps,
-            "dtype": "f64 (bf16 digit slices, exact accumulation; ~2^-40 relative per product)",
-            "roofline": {"kernel": "ozaki_gemm_kernel<EPI_FILTER>", "bound": "tensor",
-                         "achieved": 15.0 * vach, "peak": peak, "unit": "TFLOP/s",
-                         "frac": 15.0 * vach / peak, "fp64_equivalent_tflops": vach,
-                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"},
-            "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in
-                         ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid",
-                          "ms_total")},
-            "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
+    if not args.no_variant:
+        # the same step in the other precision modes, timed under the same rules:
+        # the mixed filter (split-BF16x3) and the other FP64 product path
+        variants = []
+        if prec == lib.CHASE_FP64:
+            variants.append(("variant_mixed", lib.CHASE_MIXED_BF16X3, args.fp64_tensor,
+                             args.warmup))
+            # the CUDA-core FP64 step takes over a minute at this size: one warm-up
+            variants.append(("variant_fp64_dfma" if args.fp64_tensor else "variant_fp64_tensor",
+                             lib.CHASE_FP64, 1 - args.fp64_tensor,
+                             1 if args.fp64_tensor else args.warmup))
+        for key, vprec, vt, vw in variants:
+            vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=vprec,
+                                      fp64_tensor=vt)
+            vctx, vstats, vvalue, vms, _ = timed(vprm, vw, args.steps)
+            vctx.close()
+            vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
+            line[key] = {
+                "value": vvalue, "unit": "ChASE iterations/s", "ms_per_step": vms,
+                "warmup": vw, "steps": args.steps, "dtype": dtype_name(lib, vprec, vt),
+                "fp64_tensor": vt,
+                "roofline": filter_roofline(lib, vprec, vt, vfilter, N, ne, deg),
+                "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in PHASES},
+                "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -477,12 +495,195 @@ def run_tts(args):
                   "matvecs": st["matvecs"], "matvecs_mixed": st["matvecs_mixed"],
                   "switch_iter": st["switch_iter"], "max_rel_resid": res,
                   "max_rel_eig_err": err, "phase_ms": {k: st[k] for k in (
-                      "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid")}}
+                      "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid")},
+                  "heev_sweeps": st["heev_sweeps"], "qr_variants": st["qr_variant_count"],
+                  "filter_tflops_fp64_equiv": st["filter_flops"] / (st["ms_filter"] * 1e9)}
         print(json.dumps({"mode": m, **out[m]}), file=sys.stderr, flush=True)
     line = {"metric": METRIC, "kind": "time-to-solution", "unit": "s", "higher_is_better": False,
             "config": {"workload": f"{name}: {p.spectrum} spectrum, N={N}, nev={p.nev}, "
                                    f"nex={p.nex}, tol {1e-10}"},
             "modes": out, "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_grad(args):
+    """Differentiation workload (C4: N=4096, nev=64, nex=32, uniform [0, 10] with a
+    0.05 gap after index 64): L = sum w_i lambda_i + ||X^H B X||_F^2 through the
+    autograd Function over chase_solve / chase_eig_vjp, and the filter adjoint
+    (degree 20, checkpoints every 5 steps). Times forward and backward with CUDA
+    events; checks the gradient against the oracle's exact gradient and against
+    central differences (h = 1e-6) along --grad-fd random Hermitian directions."""
+    import torch
+
+    import paper_2309_15595_gb300 as lib
+    from oracle import grad_oracle as G
+    from paper_2309_15595_gb300.autograd import chase_eigh, chebyshev_filter
+    from synth import complex_normal, config_problem, uniform01
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = config_problem("C4")
+    N = p.N
+    Ad = p.matrix_torch(dev)
+    Z = torch.from_numpy(complex_normal(4, 96, N * N).reshape(N, N)).to(dev)
+    Bt = 0.5 * (Z + Z.conj().T)
+    del Z
+    w = torch.from_numpy(uniform01(4, 97, p.nev)).to(dev)
+    V0 = torch.from_numpy(p.start_block()).to(dev)
+    Q0 = lib.colmajor(torch.from_numpy(p.lanczos_start()).to(dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def eig_step():
+        At = Ad.clone().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        lam, X, _ = chase_eigh(At, V0, p.nev, p.nex, lanczos_start=Q0,
+                               fp64_tensor=args.fp64_tensor)
+        M = X.conj().T @ Bt @ X
+        loss = torch.dot(w, lam) + torch.sum(torch.abs(M) ** 2)
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return At.grad, e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    lam_all = p.eigenvalues()
+    b_sup = lam_all[-1] * 1.01
+    c, e = (b_sup + lam_all[p.ne - 1]) / 2, (b_sup - lam_all[p.ne - 1]) / 2
+    Wt = torch.from_numpy(complex_normal(4, 98, N * p.ne).reshape(N, p.ne)).to(dev)
+
+    def filter_step():
+        At = Ad.clone().requires_grad_(True)
+        Vt = V0.clone().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        Y = chebyshev_filter(At, Vt, 20, c, e, float(lam_all[0]), checkpoint=5,
+                             fp64_tensor=args.fp64_tensor)
+        loss = torch.real(torch.sum(Wt.conj() * Y))
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    for _ in range(args.warmup):
+        eig_step()
+        filter_step()
+    eig_t = [eig_step() for _ in range(args.steps)]
+    fil_t = [filter_step() for _ in range(args.steps)]
+    Ag = eig_t[-1][0].cpu().numpy()
+    A0 = Ad.cpu().numpy()
+    B = Bt.cpu().numpy()
+    wn = w.cpu().numpy()
+    t0 = time.perf_counter()
+    lam0, X0 = G.lowest_eigenpairs(A0, p.nev)
+    ref = G.eig_vjp(A0, p.nev, wn, G.c4_loss_adjoints(lam0, X0, wn, B)[1])
+    t_oracle = time.perf_counter() - t0
+    rel = float(np.linalg.norm(Ag - ref) / np.linalg.norm(ref))
+    fd_worst = None
+    if args.grad_fd > 0:
+        h = 1e-6
+        L0 = G.c4_loss(lam0, X0, wn, B)
+        fd_worst = 0.0
+        for k in range(args.grad_fd):
+            Zk = complex_normal(4, 700 + k, N * N).reshape(N, N)
+            E = 0.5 * (Zk + Zk.conj().T)
+            E /= np.abs(np.linalg.eigvalsh(E)).max()
+            Lp = G.c4_loss(*G.lowest_eigenpairs(A0 + h * E, p.nev), wn, B)
+            Lm = G.c4_loss(*G.lowest_eigenpairs(A0 - h * E, p.nev), wn, B)
+            fd = (Lp - Lm) / (2 * h)
+            an = float(np.real(np.sum(Ag.conj() * E)))
+            fd_worst = max(fd_worst, abs(fd - an) / max(abs(an), 1e-3 * abs(L0)))
+    med = statistics.median
+    line = {"metric": METRIC, "kind": "gradient", "unit": "ms", "higher_is_better": False,
+            "config": {"workload": "C4: gap spectrum, N=4096, nev=64, nex=32; loss sum w_i "
+                                   "lambda_i + ||X^H B X||_F^2; filter adjoint degree 20, "
+                                   "checkpoint 5, on 96 columns",
+                       "fp64_tensor": args.fp64_tensor},
+            "steps": args.steps, "warmup": args.warmup,
+            "eig_forward_ms": med([t[1] for t in eig_t]),
+            "eig_backward_ms": med([t[2] for t in eig_t]),
+            "filter_forward_ms": med([t[0] for t in fil_t]),
+            "filter_backward_ms": med([t[1] for t in fil_t]),
+            "grad_rel_err_vs_oracle": rel, "oracle_gradient_s": t_oracle,
+            "fd_directions": args.grad_fd, "fd_worst_rel_mismatch": fd_worst,
+            "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batch(args):
+    """Batched warm-start sequence (C5): --batch-problems problems with N drawn
+    uniformly from [256, 4096], nev = ceil(N/20), nex = ceil(N/40), uniform
+    spectra, 8 reflectors; each solved --batch-steps times as
+    A_{t+1} = A_t + 1e-3 E_t (||E_t||_2 = 1), warm-started from the previous
+    Ritz vectors, mixed-precision filter, all problems of a step in one
+    chase_solve_batch call. Perturbations are generated outside the timed
+    region; each step's batch call is timed with CUDA events."""
+    import torch
+
+    import paper_2309_15595_gb300 as lib
+    from synth import Problem, complex_normal, uniform01
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nprob, nsteps = args.batch_problems, args.batch_steps
+    Ns = [int(256 + (4096 - 256) * u) for u in uniform01(5, 1, nprob)]
+    probs = [Problem(N=N, nev=-(-N // 20), nex=-(-N // 40), spectrum="uniform", lo=0.0,
+                     hi=10.0, reflectors=8, seed=1000 + k) for k, N in enumerate(Ns)]
+    As = [p.matrix_torch(dev) for p in probs]
+    streams = [torch.cuda.Stream(dev) for _ in probs]
+    ctxs = [lib.Context(lib.default_params(p.N, p.nev, p.nex, precision=lib.CHASE_MIXED_BF16X3,
+                                           fp64_tensor=args.fp64_tensor), s)
+            for p, s in zip(probs, streams)]
+    Vs = [lib.colmajor(torch.from_numpy(p.start_block()).to(dev)) for p in probs]
+    rz = [torch.zeros(p.ne, dtype=torch.float64, device=dev) for p in probs]
+    rs = [torch.zeros_like(r) for r in rz]
+
+    def perturb(t):
+        for k, (p, A) in enumerate(zip(probs, As)):
+            Z = torch.from_numpy(complex_normal(2000 + k, 100 + t, p.N * p.N)
+                                 .reshape(p.N, p.N)).to(dev)
+            E = 0.5 * (Z + Z.conj().T)
+            # ||E||_2 by 40 power steps on E^2 (input generation, not the method)
+            x = torch.ones(p.N, 1, dtype=E.dtype, device=dev)
+            for _ in range(40):
+                x = E @ (E @ x)
+                x /= torch.linalg.vector_norm(x)
+            E /= torch.linalg.vector_norm(E @ x)
+            A.add_(1e-3 * E)  # elementwise on the logical matrix (A keeps its strides)
+
+    step_ms, iters, mvs = [], [], []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for t in range(nsteps):
+        if t > 0:
+            perturb(t)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats, status = lib.solve_batch(ctxs, As, Vs, rz, rs, threads=args.batch_threads,
+                                        allow_not_converged=True)
+        for s in streams:
+            torch.cuda.current_stream().wait_stream(s)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(sum(st["iters"] for st in stats))
+        mvs.append(sum(st["matvecs"] for st in stats))
+    clk = clocks.stop()
+    for cx in ctxs:
+        cx.close()
+    total = sum(step_ms) / 1000.0
+    line = {"metric": METRIC, "kind": "batched warm-start sequence",
+            "value": nprob * nsteps / total, "unit": "solves/s", "higher_is_better": True,
+            "config": {"workload": f"C5: {nprob} problems, N uniform in [256, 4096], nev = "
+                                   f"ceil(N/20), nex = ceil(N/40), {nsteps} steps A += 1e-3 E, "
+                                   "warm starts, mixed filter",
+                       "threads": args.batch_threads, "fp64_tensor": args.fp64_tensor},
+            "total_s": total, "step_ms": step_ms, "iterations_per_step": iters,
+            "matvecs_per_step": mvs, "clocks": clk, "data": "synthetic"}
     print(json.dumps(line))
     return 0
 
@@ -493,6 +694,10 @@ def main():
         return run_reference(args)
     if args.tts:
         return run_tts(args)
+    if args.grad:
+        return run_grad(args)
+    if args.batch:
+        return run_batch(args)
     return run_gpu(args)
 
 

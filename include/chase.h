@@ -200,6 +200,82 @@ CHASE_API int chase_residuals_noalloc(const chase_c128* A, int64_t lda, const ch
                                       int64_t ldv, const double* ritz, int64_t N, int64_t ncols,
                                       double* resid, void* stream);
 
+/* Many independent solves at once: problem k is chase_solve(ctxs[k], A[k],
+ * lda[k], V[k], ldv[k], Q0 ? Q0[k] : NULL, ldq ? ldq[k] : 0, ritz[k],
+ * resid[k], stats ? &stats[k] : NULL), run from one of `threads` host threads
+ * (<= 0: 8; never more than count) on its context's own stream, largest
+ * N^2 (nev + nex) first, so that the kernels of different problems overlap on
+ * the GPU. Each problem's results are exactly those of chase_solve on it
+ * alone. Warm starts (a sequence of related matrices, Section 1) pass the
+ * previous Ritz vectors as V. The contexts must be distinct and should be
+ * bound to distinct streams (problems sharing a stream run one after the
+ * other); each context's device is made current on its worker thread.
+ * status[k] receives each return code; the call returns CHASE_OK if all are
+ * CHASE_OK, else the first non-OK status in problem order. The paper solves
+ * one problem at a time; this batching has no counterpart there. */
+CHASE_API int chase_solve_batch(int64_t count, struct chase_ctx* const* ctxs,
+                                const chase_c128* const* A, const int64_t* lda,
+                                chase_c128* const* V, const int64_t* ldv,
+                                const chase_c128* const* Q0, const int64_t* ldq,
+                                double* const* ritz, double* const* resid, chase_stats* stats,
+                                int32_t* status, int32_t threads);
+
+/* ---------------------------------------------------------------- gradients
+ * Adjoints for differentiating through the filter and the converged lowest
+ * eigenpairs. The paper states the forward method only (Section 2); these are
+ * its derivatives. Convention for a real loss L: the adjoint of a complex array
+ * Z is Zbar = 2 dL/d conj(Z), so dL = Re sum(conj(Zbar) dZ) (the convention
+ * torch uses). A is Hermitian, so the adjoint written for A is the Hermitian
+ * part of the unconstrained one. Both calls use the context's product path
+ * (FP64 CUDA-core or, with fp64_tensor, tensor-core FP64 for the products with
+ * A), allocate their workspace on first use (kept until chase_destroy), and
+ * synchronise the context's stream before returning. */
+
+/* Adjoint of Y = p(A) V, the Eq. 1 recurrence with the same degree `deg` for
+ * all ncols columns (Y_1 = alpha_1 (A - cI) V, Y_i = alpha_i (A - cI) Y_{i-1}
+ * + beta_i Y_{i-2}, scaled or not as the context's scaled_filter says):
+ * given Ybar (N x ncols), writes Abar (N x N) = herm(sum_i alpha_i Z_i Y_{i-1}^H)
+ * and Vbar (N x ncols) = Z_0, where Z_deg = Ybar, Z_{deg+1} = 0 and
+ * Z_{i-1} = alpha_i (A - cI) Z_i + beta_{i+1} Z_{i+1}. The states Y_i are
+ * recomputed segment by segment from checkpoints taken every `checkpoint`
+ * steps (<= 0: ceil(sqrt(deg))), so the workspace holds
+ * 2 ceil(deg/s) + 3 s + 2 blocks of N x ncols instead of deg + 1.
+ * All matrices column-major device arrays owned by the caller; Abar and Vbar
+ * are overwritten and must not alias A, V or Ybar. 1 <= deg <= 64,
+ * ncols <= nev + nex, e > 0 (and mu_1 <= c - e when scaled); else
+ * CHASE_ERR_INVALID_ARG. */
+CHASE_API int chase_filter_vjp(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                               const chase_c128* V, int64_t ldv, int64_t ncols, int32_t deg,
+                               double c, double e, double mu_1, const chase_c128* Ybar,
+                               int64_t ldyb, chase_c128* Abar, int64_t ldab, chase_c128* Vbar,
+                               int64_t ldvb, int32_t checkpoint);
+
+/* Adjoint of the nev lowest eigenpairs (lambda_i, x_i) of A, computed from a
+ * converged Ritz basis X (N x ne, nev <= ne <= nev + nex, columns 0..nev-1 the
+ * wanted pairs converged to the solver's tolerance, e.g. the V and ritz that
+ * chase_solve returns) and its Ritz values ritz (device, ne doubles, ascending).
+ * Given lam_bar (device, nev doubles, or NULL for 0) and X_bar (N x nev, or
+ * NULL for 0), writes
+ *   Abar = herm( sum_i (lam_bar_i x_i + y_i) x_i^H ),
+ *   y_i = sum_{j < nev, j != i} x_j (x_j^H xbar_i) / (ritz_i - ritz_j) - z_i,
+ * where z_i solves (A - ritz_i I) z_i = (I - Xw Xw^H) xbar_i on the orthogonal
+ * complement of the wanted block Xw = X[:, 0:nev] (conjugate gradients with the
+ * operator projected onto that complement, per column, to ||r|| <= cg_tol ||b||,
+ * at most cg_max_iter iterations, *cg_iters receives the count). The extra
+ * Ritz pairs nev..ne-1 give the initial guess (the Galerkin solution in their
+ * span). The first term is the Hellmann-Feynman derivative d lambda_i / dA =
+ * x_i x_i^H; the rest is first-order perturbation theory of x_i split into the
+ * wanted block and its complement, on which A - ritz_i I is positive definite
+ * when ritz_{nev-1} lies below the rest of the spectrum. The loss must not
+ * depend on the phase of each x_i, and the wanted eigenvalues must be simple.
+ * Returns CHASE_ERR_NOT_CONVERGED (Abar still written) if the solves did not
+ * reach cg_tol. */
+CHASE_API int chase_eig_vjp(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
+                            const chase_c128* X, int64_t ldx, const double* ritz, int64_t ne,
+                            int64_t nev, const double* lam_bar, const chase_c128* X_bar,
+                            int64_t ldxb, chase_c128* Abar, int64_t ldab, double cg_tol,
+                            int32_t cg_max_iter, int32_t* cg_iters);
+
 /* Alg. 5 condition estimate, host arithmetic on host arrays in the solver's
  * current column order: t' = (ritz[0]-c)/e, t = (ritz[locked]-c)/e,
  * cond = |rho(t)|^d |rho(t')|^(d_M - d), d = degs[locked],

@@ -26,7 +26,8 @@ from ._lib import (  # noqa: F401
     LIB,
 )
 
-__all__ = ["Context", "ChaseError", "colmajor", "default_params", "solve", "chase_cond_est",
+__all__ = ["Context", "ChaseError", "colmajor", "default_params", "solve", "solve_batch",
+           "chase_cond_est",
            "chase_degree_opt", "chase_status_string", "LIB"]
 
 
@@ -170,6 +171,35 @@ class Context:
                                    _vec(resid, ncols, "resid")), "chase_residuals")
 
 
+    def chase_filter_vjp(self, A, V, ncols, deg, c, e, mu_1, Ybar, Abar, Vbar, checkpoint=0):
+        a, lda = _mat(A, self.N, self.N, "A")
+        v, ldv = _mat(V, self.N, ncols, "V")
+        yb, ldyb = _mat(Ybar, self.N, ncols, "Ybar")
+        ab, ldab = _mat(Abar, self.N, self.N, "Abar")
+        vb, ldvb = _mat(Vbar, self.N, ncols, "Vbar")
+        _check(LIB.chase_filter_vjp(self._h, a, lda, v, ldv, int(ncols), int(deg), float(c),
+                                    float(e), float(mu_1), yb, ldyb, ab, ldab, vb, ldvb,
+                                    int(checkpoint)), "chase_filter_vjp")
+
+    def chase_eig_vjp(self, A, X, ritz, ne, nev, lam_bar, X_bar, Abar, cg_tol=1e-10,
+                      cg_max_iter=2000, allow_not_converged=False):
+        a, lda = _mat(A, self.N, self.N, "A")
+        x, ldx = _mat(X, self.N, ne, "X")
+        ab, ldab = _mat(Abar, self.N, self.N, "Abar")
+        lb = _vec(lam_bar, nev, "lam_bar") if lam_bar is not None else ctypes.c_void_p()
+        if X_bar is not None:
+            xb, ldxb = _mat(X_bar, self.N, nev, "X_bar")
+        else:
+            xb, ldxb = ctypes.c_void_p(), 0
+        it = ctypes.c_int32(0)
+        rc = LIB.chase_eig_vjp(self._h, a, lda, x, ldx, _vec(ritz, ne, "ritz"), int(ne), int(nev),
+                               lb, xb, ldxb, ab, ldab, float(cg_tol), int(cg_max_iter),
+                               ctypes.byref(it))
+        _check(rc, "chase_eig_vjp",
+               allow=(_lib.CHASE_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return int(it.value)
+
+
 # ------------------------------------------------------------ host helpers
 def chase_cond_est(ritz, degs, locked: int, c: float, e: float) -> float:
     r = np.ascontiguousarray(np.asarray(ritz, dtype=np.float64))
@@ -188,6 +218,44 @@ def chase_degree_opt(resid, ritz, c, e, tol_abs, deg_max, deg_extra):
                          float(e), float(tol_abs), int(deg_max), int(deg_extra),
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return out
+
+
+def solve_batch(contexts, As, Vs, ritzs, resids, lanczos_starts=None, threads=0,
+                allow_not_converged=False):
+    """chase_solve_batch: problem k solved on contexts[k] (its own stream) with
+    A = As[k], start block / result Vs[k], outputs ritzs[k], resids[k].
+    Returns (list of per-problem stats dicts, list of status codes)."""
+    n = len(contexts)
+    if not (len(As) == len(Vs) == len(ritzs) == len(resids) == n):
+        raise ValueError("one A, V, ritz and resid per context")
+    P = ctypes.c_void_p * n
+    I = ctypes.c_int64 * n
+    a, lda, v, ldv, q, ldq, rz, rs = P(), I(), P(), I(), P(), I(), P(), P()
+    for k, cx in enumerate(contexts):
+        a[k], lda[k] = _mat(As[k], cx.N, cx.N, "A")
+        v[k], ldv[k] = _mat(Vs[k], cx.N, cx.ne, "V")
+        rz[k] = _vec(ritzs[k], cx.ne, "ritz")
+        rs[k] = _vec(resids[k], cx.ne, "resid")
+        if lanczos_starts is not None:
+            q[k], ldq[k] = _mat(lanczos_starts[k], cx.N, int(cx.params.lanczos_vecs),
+                                "lanczos_start")
+    handles = P(*[cx._h.value for cx in contexts])
+    stats = (ChaseStats * n)()
+    status = (ctypes.c_int32 * n)()
+    rc = LIB.chase_solve_batch(n, handles, a, lda, v, ldv, q if lanczos_starts is not None else None,
+                               ldq if lanczos_starts is not None else None, rz, rs, stats, status,
+                               int(threads))
+    allow = (_lib.CHASE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    for k in range(n):
+        _check(status[k], f"chase_solve_batch[{k}]", allow=allow)
+    if rc != 0 and rc not in allow:
+        _check(rc, "chase_solve_batch")
+    out = []
+    for k in range(n):
+        d = stats[k].as_dict()
+        d["status"] = int(status[k])
+        out.append(d)
+    return out, [int(x) for x in status]
 
 
 def solve(A, nev: int, nex: int, V0=None, lanczos_start=None, allow_not_converged=False, **params):

@@ -83,6 +83,12 @@ SIGNATURES = {
     "chase_rayleigh_ritz": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i64, _vp]),
     "chase_residuals": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "chase_residuals_noalloc": (ctypes.c_int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp]),
+    "chase_solve_batch": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         ctypes.POINTER(ChaseStats), ctypes.POINTER(_i32), _i32]),
+    "chase_filter_vjp": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _dbl, _dbl, _dbl,
+                                        _vp, _i64, _vp, _i64, _vp, _i64, _i32]),
+    "chase_eig_vjp": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp, _i64,
+                                     _vp, _i64, _dbl, _i32, ctypes.POINTER(_i32)]),
     "chase_cond_est": (_dbl, [ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _i64, _i64, _dbl, _dbl]),
     "chase_degree_opt": (None, [ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _i64, _dbl, _dbl, _dbl,
                                 _i32, _i32, ctypes.POINTER(_i32)]),

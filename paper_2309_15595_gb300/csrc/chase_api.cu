@@ -13,42 +13,16 @@
 #include <numeric>
 #include <vector>
 
-#include "common.cuh"
-#include "mixed.cuh"
-#include "ozaki.cuh"
+#include "ctx.cuh"
 
 using namespace chase;
 
 namespace chase {
-static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+// per host thread, so concurrent solves on different threads count their own launches
+static thread_local long long g_launches = 0;
+void count_launch() { ++g_launches; }
+long long launch_count() { return g_launches; }
 }  // namespace chase
-
-struct chase_ctx {
-  chase_params p;
-  cudaStream_t stream;
-  int64_t N, ne;
-  double2* V2 = nullptr;        // N x ne, ld N  (C2 of Alg. 2)
-  double2* W = nullptr;         // N x ne, ld N  (B of Alg. 2, filter ping-pong)
-  double2* G = nullptr;         // ne x ne, ld ne
-  double2* Yeig = nullptr;      // ne x ne, ld ne
-  double2* gram_ws = nullptr;
-  size_t gram_ws_elems = 0;
-  double2* dinv = nullptr;
-  int* info = nullptr;
-  double* resid_partial = nullptr;
-  double* dscal = nullptr;
-  int* perm_d = nullptr;
-  double* host = nullptr;       // pinned: 2 ne + 16 doubles
-  JacobiWork jw{};
-  LanczosWork lw{};
-  MixedWork mw{};
-  OzakiWork ow{};
-  double* oz_partial = nullptr;  // residual partials of the tensor-core path (32-row tiles)
-  bool oz_a_valid = false;       // digits of the current solve's A are prepared
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
 
 namespace {
 
@@ -112,6 +86,8 @@ void free_ctx(chase_ctx* c) {
   mixed_free(c->mw);
   ozaki_free(c->ow);
   if (c->oz_partial) cudaFree(c->oz_partial);
+  if (c->gw) cudaFree(c->gw);
+  if (c->gd) cudaFree(c->gd);
   if (c->host) cudaFreeHost(c->host);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -147,15 +123,17 @@ int prepare_a(chase_ctx* c, const double2* A, int64_t lda) {
   return CHASE_OK;
 }
 
-// ------------------------------------------------------------------ filter
-int filter_impl(chase_ctx* c, const double2* A, int64_t lda, double2* V, int64_t ldv,
-                int64_t ncols, const int32_t* degs, double cc, double e, double mu1, int prec,
-                double* ms) {
-  if (ncols == 0) return CHASE_OK;
-  const int dmax = degs[ncols - 1];
-  // Eq. 1 coefficients (gamma_i = c), see chase_filter in chase.h
-  std::vector<double> al(dmax + 1, 0.0), be(dmax + 1, 0.0);
-  if (c->p.scaled_filter) {
+}  // namespace
+
+namespace chase {
+int ctx_prepare_a(chase_ctx* c, const double2* A, int64_t lda) { return prepare_a(c, A, lda); }
+
+void cheb_coefficients(int dmax, double cc, double e, double mu1, bool scaled,
+                       std::vector<double>& al, std::vector<double>& be) {
+  al.assign(dmax + 1, 0.0);
+  be.assign(dmax + 1, 0.0);
+  if (dmax < 1) return;
+  if (scaled) {
     const double sigma1 = e / (mu1 - cc);
     al[1] = sigma1 / e;
     double sig = sigma1;
@@ -172,6 +150,19 @@ int filter_impl(chase_ctx* c, const double2* A, int64_t lda, double2* V, int64_t
       be[i] = -1.0;
     }
   }
+}
+}  // namespace chase
+
+namespace {
+// ------------------------------------------------------------------ filter
+int filter_impl(chase_ctx* c, const double2* A, int64_t lda, double2* V, int64_t ldv,
+                int64_t ncols, const int32_t* degs, double cc, double e, double mu1, int prec,
+                double* ms) {
+  if (ncols == 0) return CHASE_OK;
+  const int dmax = degs[ncols - 1];
+  // Eq. 1 coefficients (gamma_i = c), see chase_filter in chase.h
+  std::vector<double> al, be;
+  cheb_coefficients(dmax, cc, e, mu1, c->p.scaled_filter != 0, al, be);
   PhaseTimer tm(c, ms);
   if (prec == CHASE_MIXED_BF16X3)
     return mixed_filter(c->stream, c->N, A, lda, V, ldv, ncols, degs, cc, al.data(), be.data(),
@@ -225,15 +216,30 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 // ---------------------------------------------------------------------- QR
 // One CholeskyQR pass (Alg. 3 body): G = X^H X (+ s I), G = U^H U, X = X U^-1.
 // Returns the POTRF info through *info_h (0 = success; X untouched otherwise).
+// With the tensor-core FP64 products the Gram matrix is a digit-sliced product
+// (its error is relative to each column's largest entry, so the filtered
+// block's graded column norms do no harm); X U^-1 stays an FP64 triangular
+// solve, because a fixed-point product of U^-1 (whose columns mix entries of
+// very different magnitude) would lose the small entries.
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
                 int* info_h) {
-  CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
-           c->gram_ws_elems));
+  if (c->p.fp64_tensor) {
+    Epilogue ep{};
+    ep.mode = EPI_STORE;
+    ep.Y = c->G;
+    ep.ldy = c->ne;
+    CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow));
+    CK(hermitian_part(c->stream, n, c->G, c->ne));
+  } else {
+    CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
+             c->gram_ws_elems));
+  }
   if (shift_factor > 0.0) CK(add_trace_shift(c->stream, n, c->G, c->ne, shift_factor, c->dscal));
   CK(potrf_upper(c->stream, n, c->G, c->ne, c->dinv, c->info));
   CK(trsm_right_upper(c->stream, c->N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
   CK(cudaMemcpyAsync(info_h, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (c->p.fp64_tensor) RC(ozaki_check(c->stream, c->ow));
   return CHASE_OK;
 }
 
@@ -282,8 +288,16 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
   } else {
     CK(zgemm_nn(c->stream, c->N, n, c->N, A, lda, Q, ldq, ep));
   }
-  CK(zgram(c->stream, c->N, n, n, Q, ldq, c->W, c->N, c->G, c->ne, false, c->gram_ws,
-           c->gram_ws_elems));                                                   // G = Q^H W
+  if (c->p.fp64_tensor) {                                                        // G = Q^H W
+    Epilogue eg{};
+    eg.mode = EPI_STORE;
+    eg.Y = c->G;
+    eg.ldy = c->ne;
+    CK(ozaki_gemm_general(c->stream, n, c->N, Q, ldq, true, n, c->W, c->N, eg, c->ow));
+  } else {
+    CK(zgram(c->stream, c->N, n, n, Q, ldq, c->W, c->N, c->G, c->ne, false, c->gram_ws,
+             c->gram_ws_elems));
+  }
   CK(hermitian_part(c->stream, n, c->G, c->ne));
   int sweeps = 0;
   {
@@ -310,7 +324,11 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
   e2.mode = EPI_STORE;
   e2.Y = V;
   e2.ldy = ldv;
-  CK(zgemm_nn(c->stream, c->N, n, n, Q, ldq, c->Yeig, c->ne, e2));               // V = Q Y
+  if (c->p.fp64_tensor) {                                                        // V = Q Y
+    CK(ozaki_gemm_general(c->stream, c->N, n, Q, ldq, false, n, c->Yeig, c->ne, e2, c->ow));
+    return ozaki_check(c->stream, c->ow);
+  }
+  CK(zgemm_nn(c->stream, c->N, n, n, Q, ldq, c->Yeig, c->ne, e2));
   return CHASE_OK;
 }
 
@@ -442,6 +460,7 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   if (!c) return CHASE_ERR_OOM;
   c->p = *p;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) c->device = 0;
   c->N = p->N;
   c->ne = p->nev + p->nex;
   const int64_t N = c->N, ne = c->ne;

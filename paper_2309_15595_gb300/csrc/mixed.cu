@@ -370,17 +370,19 @@ __global__ void state_to_f64_kernel(int64_t N, const float2* __restrict__ S, dou
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-bool get_encoder() {
-  if (g_encode) return true;
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                        &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn)
-    return false;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return true;
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+bool get_encoder() {  // thread-safe one-time lookup
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encoder();
+  g_encode = fn;
+  return fn != nullptr;
 }
 
 // rows x (2 Np) BF16, row-major; box = 64 (K) x box_rows.

@@ -37,6 +37,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "ozaki.cuh"
@@ -156,6 +157,7 @@ __device__ __forceinline__ int64_t brow_re(int64_t j) { return (j / CT) * TN + (
 struct Params {
   int64_t N, Np, j0, ncols;   // rows, padded K half, first active column, end column
   int64_t brows;              // rows of one B digit plane
+  int64_t arows;              // rows of one A digit plane (= N)
   const int* escale_a;        // per row: exponent e_i
   const double2* diag;        // diagonal of A, applied exactly in FP64
   const double2* Bsrc;        // right operand in FP64 (absolute columns, ld ldbs)
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int d = 0; d < OS; ++d) {
           // digit planes are stacked along rows: digit d of row r is row d * rows + r
-          tma_load_2d(smem_u32(st + d * A_TILE), &tmA, kx, (int)(d * P.N + m0), full);
+          tma_load_2d(smem_u32(st + d * A_TILE), &tmA, kx, (int)(d * P.arows + m0), full);
         }
 #pragma unroll
         for (int d = 0; d < OS; ++d) {
@@ -334,14 +336,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     double rsq[HC];
     if (go && row < P.N) {
       const double sa = ldexp(1.0, P.escale_a[row]);
-      const double2 dg = P.diag[row];
+      const double2 dg = P.diag ? P.diag[row] : make_double2(0.0, 0.0);
 #pragma unroll
       for (int jj = 0; jj < HC; ++jj) {
         const int64_t col = tile * CT + h * HC + jj;
         rsq[jj] = 0.0;
         if (col < P.j0 || col >= P.ncols) continue;
         const double sc = sa * ldexp(1.0, P.escale_b[col]);
-        const double2 b = P.Bsrc[row + col * P.ldbs];
+        const double2 b = P.diag ? P.Bsrc[row + col * P.ldbs] : make_double2(0.0, 0.0);
         const double lr = fma((double)acc[jj], 0x1p-40, (double)acc67[jj] * 0x1p-48);
         const double li = fma((double)acc[HC + jj], 0x1p-40, (double)acc67[HC + jj] * 0x1p-48);
         const double wr = fma(dg.x, b.x, fma(-dg.y, b.y, sc * lr));
@@ -415,14 +417,14 @@ __device__ __forceinline__ int scale_exp(double mx) {
 
 // Row maxima of A (column-major): amax[i] = max_k max(|Re A_ik|, |Im A_ik|),
 // as the bit pattern of a non-negative double (monotone in unsigned order).
-__global__ void rowmax_kernel(int64_t N, const double2* __restrict__ A, int64_t lda,
-                              unsigned long long* __restrict__ amax) {
+__global__ void rowmax_kernel(int64_t M, int64_t K, bool skip_diag, const double2* __restrict__ A,
+                              int64_t lda, unsigned long long* __restrict__ amax) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t k0 = (int64_t)blockIdx.y * 256, k1 = min(N, k0 + 256);
+  if (i >= M) return;
+  const int64_t k0 = (int64_t)blockIdx.y * 256, k1 = min(K, k0 + 256);
   double m = 0.0;
   for (int64_t k = k0; k < k1; ++k) {
-    if (k == i) continue;  // the diagonal is applied separately, exactly
+    if (skip_diag && k == i) continue;  // the diagonal is applied separately, exactly
     const double2 a = A[i + k * lda];
     m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
   }
@@ -440,23 +442,25 @@ __global__ void exps_kernel(int64_t n, const unsigned long long* __restrict__ mx
   if (i < n) e[i] = scale_exp(__longlong_as_double((long long)mx[i]));
 }
 
-// A -> OS digit planes, each N rows x 2 Np (row-major [Ar | Ai]), stacked.
-__global__ void slice_a_kernel(int64_t N, int64_t Np, const double2* __restrict__ A, int64_t lda,
+// A (M x K, column-major) -> OS digit planes, each M rows x 2 Np (row-major
+// [Ar | Ai]), stacked; skip_diag leaves the diagonal out (square A).
+__global__ void slice_a_kernel(int64_t M, int64_t K, int64_t Np, bool skip_diag,
+                               const double2* __restrict__ A, int64_t lda,
                                const int* __restrict__ ea, __nv_bfloat16* __restrict__ out) {
   __shared__ double2 tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     const int64_t i = i0 + tx, k = k0 + r;
-    tile[r][tx] = (i < N && k < N) ? A[i + k * lda] : make_double2(0.0, 0.0);
+    tile[r][tx] = (i < M && k < K) ? A[i + k * lda] : make_double2(0.0, 0.0);
   }
   __syncthreads();
   const int64_t ld = 2 * Np;
-  const size_t plane = (size_t)N * ld;
+  const size_t plane = (size_t)M * ld;
   for (int r = ty; r < 32; r += 8) {
     const int64_t i = i0 + r, k = k0 + tx;
-    if (i < N && k < N) {
-      const double2 a = i == k ? make_double2(0.0, 0.0) : tile[tx][r];
+    if (i < M && k < K) {
+      const double2 a = (skip_diag && i == k) ? make_double2(0.0, 0.0) : tile[tx][r];
       const double s = ldexp(1.0, -ea[i]);
       __nv_bfloat16 dr[OS], di[OS];
       digits_of(a.x * s, dr);
@@ -467,6 +471,28 @@ __global__ void slice_a_kernel(int64_t N, int64_t Np, const double2* __restrict_
         out[d * plane + i * ld + Np + k] = di[d];
       }
     }
+  }
+}
+
+// Left operand X^H for X (K x M, column-major): row i of X^H is conj(X[:, i]),
+// contiguous, so no transpose is needed. Exponents per row come from colexp.
+__global__ void slice_ct_kernel(int64_t M, int64_t K, int64_t Np, const double2* __restrict__ X,
+                                int64_t ldx, const int* __restrict__ ea,
+                                __nv_bfloat16* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (k >= K) return;
+  const double2 x = X[k + i * ldx];
+  const double s = ldexp(1.0, -ea[i]);
+  __nv_bfloat16 dr[OS], di[OS];
+  digits_of(x.x * s, dr);
+  digits_of(-x.y * s, di);
+  const int64_t ld = 2 * Np;
+  const size_t plane = (size_t)M * ld;
+#pragma unroll
+  for (int d = 0; d < OS; ++d) {
+    out[d * plane + i * ld + k] = dr[d];
+    out[d * plane + i * ld + Np + k] = di[d];
   }
 }
 
@@ -517,16 +543,19 @@ __global__ void slice_b_kernel(int64_t N, int64_t Np, int64_t brows, int64_t j0,
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-bool get_encoder() {
-  if (g_encode) return true;
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                        &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn)
-    return false;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return true;
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+bool get_encoder() {  // thread-safe one-time lookup
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encoder();
+  g_encode = fn;
+  return fn != nullptr;
 }
 bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows) {
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * Np), (cuuint64_t)rows};
@@ -566,6 +595,12 @@ cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne) {
   if ((e = cudaMalloc(&w.diag, N * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.err, sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMemset(w.err, 0, sizeof(int))) != cudaSuccess) return e;
+  // general left operands of the N x n^2 products: X^H (ne x N) or Q (N x ne)
+  const int64_t npe = ozaki_np(ne);
+  w.l_elems = (size_t)OS * std::max((size_t)ne * 2 * w.Np, (size_t)N * 2 * npe);
+  if ((e = cudaMalloc(&w.Ld, w.l_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.Ld, 0, w.l_elems * 2)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.el, std::max(N, ne) * sizeof(int))) != cudaSuccess) return e;
   Maps* maps = nullptr;
   if ((e = cudaMallocHost(&maps, sizeof(Maps))) != cudaSuccess) return e;
   w.maps = maps;
@@ -578,7 +613,7 @@ cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne) {
 }
 
 void ozaki_free(OzakiWork& w) {
-  void* bufs[] = {w.Ad, w.Bd, w.ea, w.eb, w.amax, w.err, w.diag};
+  void* bufs[] = {w.Ad, w.Bd, w.ea, w.eb, w.amax, w.err, w.diag, w.Ld, w.el};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (w.maps) cudaFreeHost(w.maps);
@@ -589,15 +624,15 @@ cudaError_t ozaki_prepare_a(cudaStream_t s, const double2* A, int64_t lda, Ozaki
   const int64_t N = w.N;
   cudaError_t e = cudaMemsetAsync(w.amax, 0, N * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  rowmax_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)cdiv(N, 256), 1), 256, 0, s>>>(N, A, lda,
-                                                                                        w.amax);
+  rowmax_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)cdiv(N, 256), 1), 256, 0, s>>>(
+      N, N, true, A, lda, w.amax);
   count_launch();
   exps_kernel<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(N, w.amax, w.ea);
   count_launch();
   diag_kernel<<<(unsigned)cdiv(N, 256), 256, 0, s>>>(N, A, lda, w.diag);
   count_launch();
   slice_a_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(N, 32), 1), dim3(32, 8, 1), 0, s>>>(
-      N, w.Np, A, lda, w.ea, static_cast<__nv_bfloat16*>(w.Ad));
+      N, N, w.Np, true, A, lda, w.ea, static_cast<__nv_bfloat16*>(w.Ad));
   count_launch();
   w.A_ready = A;
   return cudaGetLastError();
@@ -619,6 +654,7 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
   P.N = N;
   P.Np = w.Np;
   P.brows = w.brows;
+  P.arows = N;
   P.j0 = j0;
   P.ncols = ncols_end;
   P.escale_a = w.ea;
@@ -639,6 +675,79 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
   P.err = w.err;
   const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / CT - j0 / CT + 1), 1);
   ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const double2* X,
+                               int64_t ldx, bool conj_trans, int64_t ncols, const double2* B,
+                               int64_t ldb, const Epilogue& ep, OzakiWork& w) {
+  if (M <= 0 || ncols <= 0 || K <= 0) return cudaSuccess;
+  const int64_t Kp = ozaki_np(K);
+  if (Kp > w.Np || ncols > w.ne || (size_t)OS * M * 2 * Kp > w.l_elems)
+    return cudaErrorInvalidValue;
+  __nv_bfloat16* L = static_cast<__nv_bfloat16*>(w.Ld);
+  // The K padding of the left planes must be zero (the right operand's padding
+  // then only has to be finite, which digits always are). The slicing writes
+  // k < K only, so the planes are cleared whenever their layout changes.
+  cudaError_t e;
+  if (M != w.l_M || K != w.l_K) {
+    if ((e = cudaMemsetAsync(L, 0, (size_t)OS * M * 2 * Kp * 2, s)) != cudaSuccess) return e;
+    w.l_M = M;
+    w.l_K = K;
+  }
+  if (conj_trans) {  // left = X^H, X is K x M
+    colexp_kernel<<<(unsigned)M, 256, 0, s>>>(K, 0, X, ldx, w.el);
+    count_launch();
+    slice_ct_kernel<<<dim3((unsigned)cdiv(K, 256), (unsigned)M, 1), 256, 0, s>>>(M, K, Kp, X, ldx,
+                                                                                 w.el, L);
+    count_launch();
+  } else {           // left = X, M x K
+    if ((e = cudaMemsetAsync(w.amax, 0, M * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    rowmax_kernel<<<dim3((unsigned)cdiv(M, 256), (unsigned)cdiv(K, 256), 1), 256, 0, s>>>(
+        M, K, false, X, ldx, w.amax);
+    count_launch();
+    exps_kernel<<<(unsigned)cdiv(M, 256), 256, 0, s>>>(M, w.amax, w.el);
+    count_launch();
+    slice_a_kernel<<<dim3((unsigned)cdiv(M, 32), (unsigned)cdiv(K, 32), 1), dim3(32, 8, 1), 0, s>>>(
+        M, K, Kp, false, X, ldx, w.el, L);
+    count_launch();
+  }
+  // right operand digits, K rows
+  colexp_kernel<<<(unsigned)ncols, 256, 0, s>>>(K, 0, B, ldb, w.eb);
+  count_launch();
+  slice_b_kernel<<<dim3((unsigned)cdiv(K, 256), (unsigned)ncols, 1), 256, 0, s>>>(
+      K, Kp, w.brows, 0, B, ldb, w.eb, static_cast<__nv_bfloat16*>(w.Bd));
+  count_launch();
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, L, (int64_t)OS * M, Kp, TM) ||
+      !make_map(&mb, w.Bd, (int64_t)OS * w.brows, Kp, TN))
+    return cudaErrorInvalidValue;
+  Params P;
+  P.N = M;
+  P.Np = Kp;
+  P.brows = w.brows;
+  P.arows = M;
+  P.j0 = 0;
+  P.ncols = ncols;
+  P.escale_a = w.el;
+  P.escale_b = w.eb;
+  P.diag = nullptr;
+  P.Bsrc = B;
+  P.ldbs = ldb;
+  P.mode = ep.mode;
+  P.alpha = ep.alpha;
+  P.beta = ep.beta;
+  P.gamma = ep.gamma;
+  P.X = ep.X;
+  P.ldx = ep.ldx;
+  P.Y = ep.Y;
+  P.ldy = ep.ldy;
+  P.theta = ep.theta;
+  P.partial = ep.partial;
+  P.err = w.err;
+  const dim3 grid((unsigned)cdiv(M, TM), (unsigned)((ncols - 1) / CT + 1), 1);
+  ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, P);
   count_launch();
   return cudaGetLastError();
 }

@@ -16,6 +16,10 @@ struct OzakiWork {
   int* err = nullptr;
   void* maps = nullptr;         // TMA tensor maps (pinned host)
   const void* A_ready = nullptr;  // A whose digits are in Ad
+  void* Ld = nullptr;           // digit planes of a general left operand (N x n^2 products)
+  size_t l_elems = 0;
+  int* el = nullptr;            // row exponents of the general left operand
+  int64_t l_M = 0, l_K = 0;     // layout of the planes in Ld (0: not yet written)
   int64_t N = 0, ne = 0, Np = 0, brows = 0;
 };
 
@@ -29,6 +33,12 @@ cudaError_t ozaki_prepare_a(cudaStream_t s, const double2* A, int64_t lda, Ozaki
 // column, indexed by absolute column). Y, X, theta, partial use absolute columns.
 cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const double2* B,
                        int64_t ldb, const Epilogue& ep, OzakiWork& w);
+// P = op(X) * B for the N x n^2 products: op(X) = X (M x K, column-major) or,
+// with conj_trans, X^H for X of K x M; B is K x ncols. No diagonal split. The
+// epilogue uses absolute columns 0 .. ncols of B, X, Y. K <= N, ncols <= ne.
+cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const double2* X,
+                               int64_t ldx, bool conj_trans, int64_t ncols, const double2* B,
+                               int64_t ldb, const Epilogue& ep, OzakiWork& w);
 // Reads and clears the device error flag; returns a chase_status.
 int ozaki_check(cudaStream_t s, OzakiWork& w);
 

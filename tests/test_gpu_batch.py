@@ -1,0 +1,96 @@
+"""Many independent problems in one chase_solve_batch call, and warm starts
+along a sequence of perturbed matrices (A_{t+1} = A_t + 1e-3 E_t, ||E_t||_2 = 1).
+
+The batch runs each problem on its own context and stream from a host thread
+pool; the kernels and their reduction orders are those of a single solve, so
+the batched results must equal the one-at-a-time results bit for bit.
+"""
+import numpy as np
+import pytest
+
+from synth import Problem, complex_normal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(x, lib):
+    return lib.colmajor(torch.from_numpy(np.asfortranarray(x)).cuda())
+
+
+def batch_problem(N, seed):
+    # nev = ceil(N/20), nex = ceil(N/40), uniform spectrum, 8 reflectors
+    return Problem(N=N, nev=-(-N // 20), nex=-(-N // 40), spectrum="uniform", lo=0.0,
+                   hi=10.0, reflectors=8, seed=seed)
+
+
+def unit_hermitian(N, seed):
+    Z = complex_normal(seed, 95, N * N).reshape(N, N)
+    E = 0.5 * (Z + Z.conj().T)
+    return E / np.abs(np.linalg.eigvalsh(E)).max()
+
+
+@pytest.mark.parametrize("tensor,precision", [(0, 0), (1, 1)])
+def test_batch_equals_single_solves(lib, tensor, precision):
+    sizes = [256, 700, 384, 1000, 300]
+    probs = [batch_problem(N, 40 + k) for k, N in enumerate(sizes)]
+    As = [dev(p.matrix(), lib) for p in probs]
+
+    def run(batched):
+        ctxs, Vs, rz, rs = [], [], [], []
+        streams = [torch.cuda.Stream() for _ in probs]
+        for p, s in zip(probs, streams):
+            prm = lib.default_params(p.N, p.nev, p.nex, fp64_tensor=tensor, precision=precision)
+            ctxs.append(lib.Context(prm, s))
+            Vs.append(dev(p.start_block(), lib))
+            rz.append(torch.zeros(p.ne, dtype=torch.float64, device="cuda"))
+            rs.append(torch.zeros(p.ne, dtype=torch.float64, device="cuda"))
+        Q0 = [dev(p.lanczos_start(), lib) for p in probs]
+        torch.cuda.synchronize()
+        if batched:
+            stats, status = lib.solve_batch(ctxs, As, Vs, rz, rs, lanczos_starts=Q0, threads=3)
+        else:
+            stats = [cx.chase_solve(A, V, r, s, lanczos_start=q)
+                     for cx, A, V, r, s, q in zip(ctxs, As, Vs, rz, rs, Q0)]
+            status = [st["status"] for st in stats]
+        torch.cuda.synchronize()
+        for cx in ctxs:
+            cx.close()
+        return ([v.cpu().numpy() for v in Vs], [r.cpu().numpy() for r in rz],
+                [r.cpu().numpy() for r in rs], stats, status)
+
+    Vb, rzb, rsb, stb, sb = run(True)
+    Vs, rzs, rss, sts, ss = run(False)
+    assert sb == ss == [0] * len(probs)
+    for k, p in enumerate(probs):
+        assert np.array_equal(rzb[k], rzs[k]), k
+        assert np.array_equal(rsb[k], rss[k]), k
+        assert np.array_equal(Vb[k], Vs[k]), k
+        assert stb[k]["matvecs"] == sts[k]["matvecs"]
+        lam = p.eigenvalues()[:p.nev]
+        assert np.abs(rzb[k][:p.nev] - lam).max() <= 1e-10 * p.norm2()
+
+
+def test_warm_start_sequence(lib):
+    p = batch_problem(800, 77)
+    A0 = p.matrix()
+    Ad = dev(A0, lib)
+    prm = lib.default_params(p.N, p.nev, p.nex)
+    with lib.Context(prm) as cx:
+        V = dev(p.start_block(), lib)
+        rz = torch.zeros(p.ne, dtype=torch.float64, device="cuda")
+        rs = torch.zeros_like(rz)
+        cold0 = cx.chase_solve(Ad, V, rz, rs)
+        A = A0
+        for t in range(3):
+            A = A + 1e-3 * unit_hermitian(p.N, 500 + t)
+            Ad = dev(A, lib)
+            Vc = dev(p.start_block(), lib)
+            cold = cx.chase_solve(Ad, Vc, rz, rs)
+            warm = cx.chase_solve(Ad, V, rz, rs)  # V: the previous step's Ritz vectors
+            lam = np.linalg.eigvalsh(A)[:p.nev]
+            nA = np.abs(np.linalg.eigvalsh(A)).max()
+            assert np.abs(rz.cpu().numpy()[:p.nev] - lam).max() <= 1e-10 * nA
+            print(f"step {t}: matvecs cold {cold['matvecs']} warm {warm['matvecs']} "
+                  f"(first cold solve {cold0['matvecs']})")
+            assert warm["matvecs"] < cold["matvecs"]

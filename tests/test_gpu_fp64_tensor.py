@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import chase_oracle as O
-from synth import Problem, config_problem
+from synth import Problem, complex_normal, config_problem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,7 +53,47 @@ def test_tensor_fp64_filter_against_oracle(lib, N, ncols, dmax):
     assert np.all(rel <= degs * 2.0 ** -42)
 
 
-@pytest.mark.parametrize("N,n", [(400, 30), (300, 65)])
+def matrix_with_cond(m, n, kappa, seed):
+    U = np.linalg.qr(complex_normal(seed, 78, m * n).reshape(n, m).T)[0]
+    W = np.linalg.qr(complex_normal(seed + 1, 77, n * n).reshape(n, n))[0]
+    s = np.logspace(0, -np.log10(kappa), n)
+    return np.asfortranarray((U * s[None, :]) @ W.conj().T)
+
+
+@pytest.mark.parametrize("m,n,kappa,graded", [
+    (400, 24, 5.0, 0), (333, 37, 1e4, 0), (700, 150, 1e6, 0), (500, 40, 1e11, 0),
+    (300, 20, 1e15, 0), (129, 129, 10.0, 0), (600, 60, 1e10, 1), (400, 48, 1e6, 1)])
+def test_tensor_fp64_qr(lib, m, n, kappa, graded):
+    # Gram matrix X^H X as a digit-sliced product: error about sqrt(m) 2^-47 of
+    # the column maxima instead of sqrt(m) 2^-53, so the unique (positive
+    # diag R) Q matches the oracle to 1e-12 kappa instead of 1e-13 kappa; the
+    # orthogonality bar stays 1e-12. graded: columns scaled over `kappa` like a
+    # filtered block (column norms from T_d of the Ritz values).
+    if graded:
+        X = matrix_with_cond(m, n, 10.0, 7) * np.logspace(0, np.log10(kappa), n)[None, :]
+        X = np.asfortranarray(X)
+    else:
+        X = matrix_with_cond(m, n, kappa, 7)
+    Qo, vo, _ = O.caqr(X, kappa)
+    with lib.Context(lib.default_params(m, n, 0, fp64_tensor=1)) as ctx:
+        Xd = dev(X, lib)
+        v = ctx.chase_qr(Xd, n, kappa)
+        Q = Xd.cpu().numpy()
+    orth = np.abs(Q.conj().T @ Q - np.eye(n)).max()
+    print(f"m={m} n={n} kappa={kappa:.0e}: variant {v} (oracle {vo}), orth {orth:.2e}, "
+          f"vs oracle {np.abs(Q - Qo).max():.2e}")
+    if kappa <= 1e6:
+        assert v == vo
+        assert np.abs(Q - Qo).max() <= 1e-12 * kappa * 10
+    else:
+        assert v in (3, 4)
+    assert orth <= 1e-12
+    R = Q.conj().T @ X
+    assert np.abs(np.tril(R, -1)).max() <= 1e-12 * max(1.0, kappa * 1e-3) * np.abs(R).max()
+    assert np.all(np.diag(R).real > 0)
+
+
+@pytest.mark.parametrize("N,n", [(400, 30), (300, 65), (600, 129)])
 def test_tensor_fp64_rayleigh_ritz_and_residuals(lib, N, n):
     p = Problem(N=N, nev=n - n // 4, nex=n // 4, spectrum="uniform", lo=0.5, hi=9.0,
                 reflectors=6, seed=N + n)
@@ -72,6 +112,8 @@ def test_tensor_fp64_rayleigh_ritz_and_residuals(lib, N, n):
         r = resid.cpu().numpy()
     assert np.abs(th - th_o).max() <= 1e-12 * p.norm2()
     np.testing.assert_allclose(r, r_o, rtol=1e-9)
+    V = Vd.cpu().numpy()
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() <= 1e-12
 
 
 @pytest.mark.parametrize("precision", [0, 1])
