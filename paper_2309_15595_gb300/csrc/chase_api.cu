@@ -216,14 +216,17 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 // ---------------------------------------------------------------------- QR
 // One CholeskyQR pass (Alg. 3 body): G = X^H X (+ s I), G = U^H U, X = X U^-1.
 // Returns the POTRF info through *info_h (0 = success; X untouched otherwise).
-// With the tensor-core FP64 products the Gram matrix is a digit-sliced product
-// (its error is relative to each column's largest entry, so the filtered
-// block's graded column norms do no harm); X U^-1 stays an FP64 triangular
-// solve, because a fixed-point product of U^-1 (whose columns mix entries of
-// very different magnitude) would lose the small entries.
+// With the tensor-core FP64 products, the Gram matrix of every pass but the
+// last is a digit-sliced product (error about sqrt(N) 2^-47 of the column
+// maxima; the next pass removes what it leaves). The last pass of a variant
+// fixes the orthogonality, which is about kappa(X)^2 times the Gram error, so
+// it keeps the FP64 CUDA-core Gram. X U^-1 is always the FP64 triangular
+// solve: a fixed-point product with U^-1 (whose columns mix entries of very
+// different magnitude for a filtered block) would lose the small entries.
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
-                int* info_h) {
-  if (c->p.fp64_tensor) {
+                bool last, int* info_h) {
+  const bool tc = c->p.fp64_tensor && !last;
+  if (tc) {
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = c->G;
@@ -239,7 +242,7 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
   CK(trsm_right_upper(c->stream, c->N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
   CK(cudaMemcpyAsync(info_h, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (c->p.fp64_tensor) RC(ozaki_check(c->stream, c->ow));
+  if (tc) RC(ozaki_check(c->stream, c->ow));
   return CHASE_OK;
 }
 
@@ -250,7 +253,7 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
     const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
     bool ok = true;
     for (int k = 0; k < passes && ok; ++k) {
-      RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
+      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, info_h));
       ok = (*info_h == 0);
     }
     if (ok) {
@@ -262,10 +265,10 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
   // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2
   const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
   for (int attempt = 0; attempt < 3; ++attempt) {
-    RC(cholqr_pass(c, X, ldx, n, factor, info_h));
+    RC(cholqr_pass(c, X, ldx, n, factor, false, info_h));
     if (*info_h != 0) return CHASE_ERR_QR_BREAKDOWN;
-    RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
-    if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, info_h));
+    RC(cholqr_pass(c, X, ldx, n, 0.0, false, info_h));
+    if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, info_h));
     if (*info_h == 0) {
       if (variant) *variant = attempt == 0 ? CHASE_QR_SHIFTED : CHASE_QR_FALLBACK;
       return CHASE_OK;
