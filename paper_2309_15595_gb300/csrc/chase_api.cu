@@ -597,7 +597,15 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   double2* C = reinterpret_cast<double2*>(Vc);
   chase_stats st;
   std::memset(&st, 0, sizeof(st));
-  cudaEvent_t t_start, t_end;
+  cudaEvent_t t_start = nullptr, t_end = nullptr;
+  struct EventGuard {  // released on every return path
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~EventGuard() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } event_guard{&t_start, &t_end};
   CK(cudaEventCreate(&t_start));
   CK(cudaEventCreate(&t_end));
   CK(cudaEventRecord(t_start, c->stream));
@@ -758,8 +766,6 @@ int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc,
   CK(cudaStreamSynchronize(c->stream));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, t_start, t_end);
-  cudaEventDestroy(t_start);
-  cudaEventDestroy(t_end);
   st.ms_total = ms;
   st.iters = iter - 1;
   st.locked = (int32_t)locked;

@@ -484,6 +484,28 @@ __global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs<T> a) {
     if (decide == 1) { conv = true; break; }
     if (decide == 2) break;
     for (int round = 0; round < a.m - 1; ++round) {
+      if constexpr (sizeof(T) == 4) {
+        // FP32: every block computes all of this round's rotations itself (cheap
+        // in FP32), which saves the grid barrier between computing and applying
+        for (int k = threadIdx.x; k < npairs; k += LJ_T) {
+          int p, q;
+          rr_pair(a.m, round, k, p, q);
+          const RotT<T> r = q < n ? make_rot_t<T>(Gcur[p + (int64_t)p * n].x,
+                                                  Gcur[q + (int64_t)q * n].x,
+                                                  Gcur[p + (int64_t)q * n])
+                                  : make_rot_t<T>(T(0), T(0), Cx<T>::mk(T(0), T(0)));
+          T* pp = sparams + 8 * k;
+          pp[0] = r.c; pp[1] = r.s; pp[2] = r.px; pp[3] = r.py; pp[4] = r.app; pp[5] = r.aqq;
+        }
+        __syncthreads();
+        for (int k = blockIdx.x; k < npairs; k += gridDim.x)
+          process_pair<T>(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf, sparams, sparams);
+        if (!grid_sync(a.bar, a.status)) { alive = false; break; }
+        C* t = Gcur;
+        Gcur = Gnxt;
+        Gnxt = t;
+        continue;
+      }
       for (int k = blockIdx.x * LJ_T + threadIdx.x; k < npairs; k += gridDim.x * LJ_T) {
         int p, q;
         rr_pair(a.m, round, k, p, q);
