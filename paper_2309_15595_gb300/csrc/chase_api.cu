@@ -357,6 +357,13 @@ int resid_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* V, in
 }
 
 // Lanczos block product on the tensor cores (digits of A prepared by the caller).
+cudaError_t heev_tensor_gemm(void* vc, int64_t M, int64_t K, const double2* X, int64_t ldx,
+                             bool conj_trans, int64_t ncols, const double2* B, int64_t ldb,
+                             const Epilogue& ep) {
+  chase_ctx* c = static_cast<chase_ctx*>(vc);
+  return ozaki_gemm_general(c->stream, M, K, X, ldx, conj_trans, ncols, B, ldb, ep, c->ow);
+}
+
 cudaError_t lanczos_tensor_matmul(void* vc, const double2* Q, int64_t ldq, int nvec, double2* W,
                                   int64_t ldw) {
   chase_ctx* c = static_cast<chase_ctx*>(vc);
@@ -515,6 +522,10 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
     c->jw.gram_ws_elems = c->gram_ws_elems;
     c->jw.dinv = c->dinv;
     c->jw.info = c->info;
+    if (p->fp64_tensor) {  // the heev's FP64 refinement products on the tensor cores
+      c->jw.gemm = heev_tensor_gemm;
+      c->jw.gemm_ctx = c;
+    }
   }
   if (!ok) {
     cudaGetLastError();

@@ -94,6 +94,22 @@ cudaError_t trsm_right_upper(cudaStream_t s, int64_t m, int64_t n, double2* X, i
 cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double factor,
                             double* scratch);
 
+// Grouped raster order of an nrow x ncol grid of output tiles: consecutive CTAs
+// take `group` row blocks of one column tile, then the same row blocks of the
+// next column tile, so the CTAs resident at one time read a few row blocks of
+// the left operand and a few column tiles of the right one, and L2 serves each
+// tile to the rest of the wave instead of DRAM. Bijective on [0, nrow ncol).
+__device__ __forceinline__ void grouped_tile(unsigned id, unsigned nrow, unsigned ncol,
+                                             unsigned group, unsigned& row, unsigned& col) {
+  const unsigned per = group * ncol;
+  const unsigned g = id / per;
+  const unsigned first = g * group;
+  const unsigned rg = min(group, nrow - first);
+  const unsigned local = id - g * per;
+  row = first + local % rg;
+  col = local / rg;
+}
+
 // ------------------------------------------------------------ eigensolver
 // Two-sided cyclic Jacobi with round-robin parallel ordering on the n x n
 // Hermitian G (destroyed). Eigenvalues ascending into w (device), eigenvectors
@@ -115,6 +131,12 @@ struct JacobiWork {
   double* red;       // reduction scratch
   double* host_red;  // pinned host scalars
   int64_t nmax;
+  // optional product for the FP64 refinement: P = op(X) B (op(X) = X, M x K, or
+  // X^H for X of K x M), epilogue as for zgemm_nn; null: CUDA-core FP64 products
+  cudaError_t (*gemm)(void* ctx, int64_t M, int64_t K, const double2* X, int64_t ldx,
+                      bool conj_trans, int64_t ncols, const double2* B, int64_t ldb,
+                      const Epilogue& ep) = nullptr;
+  void* gemm_ctx = nullptr;
 };
 size_t jacobi_params_elems(int64_t n);
 size_t jacobi_red_elems();  // doubles of JacobiWork::red

@@ -270,13 +270,6 @@ __device__ __forceinline__ RotT<T> load_rot_t(const T* __restrict__ params, int 
   return r;
 }
 
-__global__ void init_kernel(int64_t n, const double2* G, int64_t ldg, double2* Gw, double2* Zw) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y;
-  if (i >= n) return;
-  Gw[i + j * n] = G[i + j * ldg];
-  Zw[i + j * n] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-}
 __global__ void init32_kernel(int64_t n, const double2* G, int64_t ldg, float2* G32, float2* Z32) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = blockIdx.y;
@@ -500,26 +493,25 @@ __global__ void __launch_bounds__(LJ_T) jacobi_coop_kernel(CoopArgs<T> a) {
         __syncthreads();
         for (int k = blockIdx.x; k < npairs; k += gridDim.x)
           process_pair<T>(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf, sparams, sparams);
+      } else {
+        // FP64 rotations are expensive on this part: computed once (phase A),
+        // published through global memory, then applied (phase B)
+        for (int k = blockIdx.x * LJ_T + threadIdx.x; k < npairs; k += gridDim.x * LJ_T) {
+          int p, q;
+          rr_pair(a.m, round, k, p, q);
+          const RotT<T> r = q < n ? make_rot_t<T>(Gcur[p + (int64_t)p * n].x,
+                                                  Gcur[q + (int64_t)q * n].x,
+                                                  Gcur[p + (int64_t)q * n])
+                                  : make_rot_t<T>(T(0), T(0), Cx<T>::mk(T(0), T(0)));
+          T* pp = a.params + 8 * k;
+          pp[0] = r.c; pp[1] = r.s; pp[2] = r.px; pp[3] = r.py; pp[4] = r.app; pp[5] = r.aqq;
+        }
         if (!grid_sync(a.bar, a.status)) { alive = false; break; }
-        C* t = Gcur;
-        Gcur = Gnxt;
-        Gnxt = t;
-        continue;
+        for (int e = threadIdx.x; e < 8 * npairs; e += LJ_T) sparams[e] = a.params[e];
+        __syncthreads();
+        for (int k = blockIdx.x; k < npairs; k += gridDim.x)
+          process_pair<T>(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf, a.params, sparams);
       }
-      for (int k = blockIdx.x * LJ_T + threadIdx.x; k < npairs; k += gridDim.x * LJ_T) {
-        int p, q;
-        rr_pair(a.m, round, k, p, q);
-        const RotT<T> r = q < n ? make_rot_t<T>(Gcur[p + (int64_t)p * n].x, Gcur[q + (int64_t)q * n].x,
-                                                Gcur[p + (int64_t)q * n])
-                                : make_rot_t<T>(T(0), T(0), Cx<T>::mk(T(0), T(0)));
-        T* pp = a.params + 8 * k;
-        pp[0] = r.c; pp[1] = r.s; pp[2] = r.px; pp[3] = r.py; pp[4] = r.app; pp[5] = r.aqq;
-      }
-      if (!grid_sync(a.bar, a.status)) { alive = false; break; }
-      for (int e = threadIdx.x; e < 8 * npairs; e += LJ_T) sparams[e] = a.params[e];
-      __syncthreads();
-      for (int k = blockIdx.x; k < npairs; k += gridDim.x)
-        process_pair<T>(n, a.m, round, k, Gcur, Gnxt, a.Z, colbuf, a.params, sparams);
       if (!grid_sync(a.bar, a.status)) { alive = false; break; }
       C* t = Gcur;
       Gcur = Gnxt;
@@ -615,11 +607,160 @@ __global__ void permute_cols_kernel(int64_t n, const double2* Zw, const int* ran
   Z[i + (int64_t)rank[c] * ldz] = Zw[i + c * n];
 }
 
+// ------------------------------------------ FP64 refinement of the FP32 pairs
+// One step of the iterative refinement of Ogita and Aishima (2018) for an
+// approximate eigenvector matrix X of Hermitian G, with S = X^H G X and
+// R = I - X^H X: lambda_i = Re s_ii / (1 - Re r_ii) and
+// E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) (i != j), E_ii = r_ii / 2,
+// then X <- X (I + E). Quadratic convergence from the FP32 Jacobi vectors. A
+// pair whose first-order correction would exceed 1e-3 (eigenvalues too close
+// to separate at this accuracy; larger corrections made near-degenerate pairs
+// oscillate in tests) is only orthogonalised (E_ij = r_ij / 2); the largest
+// |s_ij| of such pairs is reported so that FP64 Jacobi sweeps can finish them.
+__global__ void oa_lambda_kernel(int64_t n, const double2* __restrict__ S,
+                                 const double2* __restrict__ XX, double* __restrict__ lam) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  lam[i] = S[i + i * n].x / XX[i + i * n].x;  // 1 - r_ii = (X^H X)_ii
+}
+__global__ void oa_e_kernel(int64_t n, const double2* __restrict__ S,
+                            const double2* __restrict__ XX, const double* __restrict__ lam,
+                            double2* __restrict__ E, double* __restrict__ partial) {
+  __shared__ double me[256], mc[256];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // row
+  const int64_t j = blockIdx.y;                                        // column
+  double emax = 0.0, cmax = 0.0;
+  if (i < n) {
+    const double2 x = XX[i + j * n];
+    const double2 r = make_double2((i == j ? 1.0 : 0.0) - x.x, -x.y);
+    double2 e;
+    if (i == j) {
+      e = make_double2(0.5 * r.x, 0.5 * r.y);
+      emax = 0.5 * sqrt(r.x * r.x + r.y * r.y);
+    } else {
+      const double2 sv = S[i + j * n];
+      const double lj = lam[j], d = lj - lam[i];
+      const double2 num = make_double2(fma(lj, r.x, sv.x), fma(lj, r.y, sv.y));
+      const double an = sqrt(num.x * num.x + num.y * num.y);
+      if (an <= 1e-3 * fabs(d)) {
+        e = make_double2(num.x / d, num.y / d);
+        emax = an / fabs(d);
+      } else {
+        e = make_double2(0.5 * r.x, 0.5 * r.y);
+        emax = 0.5 * sqrt(r.x * r.x + r.y * r.y);
+        cmax = sqrt(sv.x * sv.x + sv.y * sv.y);
+      }
+    }
+    E[i + j * n] = e;
+  }
+  me[threadIdx.x] = emax;
+  mc[threadIdx.x] = cmax;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) {
+      me[threadIdx.x] = fmax(me[threadIdx.x], me[threadIdx.x + w]);
+      mc[threadIdx.x] = fmax(mc[threadIdx.x], mc[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+    partial[2 * b] = me[0];
+    partial[2 * b + 1] = mc[0];
+  }
+}
+// E = (I - XX) / 2: one orthogonalisation step X <- X (I + E)
+__global__ void half_residual_kernel(int64_t n, const double2* __restrict__ XX,
+                                     double2* __restrict__ E) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const double2 x = XX[i + j * n];
+  E[i + j * n] = make_double2(0.5 * ((i == j ? 1.0 : 0.0) - x.x), -0.5 * x.y);
+}
+__global__ void max2_kernel(int64_t nb, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double a[256], c[256];
+  double x = 0.0, y = 0.0;
+  for (int64_t b = threadIdx.x; b < nb; b += 256) {
+    x = fmax(x, partial[2 * b]);
+    y = fmax(y, partial[2 * b + 1]);
+  }
+  a[threadIdx.x] = x;
+  c[threadIdx.x] = y;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) {
+      a[threadIdx.x] = fmax(a[threadIdx.x], a[threadIdx.x + w]);
+      c[threadIdx.x] = fmax(c[threadIdx.x], c[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = a[0];
+    out[1] = c[0];
+  }
+}
+__global__ void rank_vec_kernel(int64_t n, const double* __restrict__ lam, double* w, int* rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = lam[i];
+  int64_t rk = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const double u = lam[j];
+    rk += (u < v) || (u == v && j < i);
+  }
+  rank[i] = (int)rk;
+  w[rk] = v;
+}
+__global__ void frob2_kernel(int64_t n, const double2* __restrict__ G, int64_t ldg,
+                             double* __restrict__ partial) {
+  __shared__ double a[256];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  double v = 0.0;
+  if (i < n) {
+    const double2 g = G[i + j * ldg];
+    v = g.x * g.x + g.y * g.y;
+  }
+  a[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) a[threadIdx.x] += a[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+    partial[2 * b] = sqrt(a[0]);  // max of column-block norms: a cheap scale of ||G||
+    partial[2 * b + 1] = 0.0;
+  }
+}
+
 bool g_small_attr = false;
 
 }  // namespace
 
 size_t jacobi_red_elems() { return (size_t)2 * kCoopMaxGrid + 16; }
+
+namespace {
+// refinement products: P = A B (n x n) or P = X^H Y, on the tensor cores when
+// the context supplied a product, else with the CUDA-core kernels
+cudaError_t heev_nn(cudaStream_t s, const JacobiWork& wk, int64_t n, const double2* A,
+                    int64_t lda, const double2* B, const Epilogue& ep) {
+  if (wk.gemm) return wk.gemm(wk.gemm_ctx, n, n, A, lda, false, n, B, n, ep);
+  return zgemm_nn(s, n, n, n, A, lda, B, n, ep);
+}
+cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, int64_t n, const double2* X,
+                    const double2* Y, double2* P, bool hermitian) {
+  if (wk.gemm) {
+    Epilogue ep{};
+    ep.mode = EPI_STORE;
+    ep.Y = P;
+    ep.ldy = n;
+    cudaError_t e = wk.gemm(wk.gemm_ctx, n, n, X, n, true, n, Y, n, ep);
+    if (e != cudaSuccess || !hermitian) return e;
+    return hermitian_part(s, n, P, n);
+  }
+  return zgram(s, n, n, n, X, n, Y, n, P, n, hermitian, wk.gram_ws, wk.gram_ws_elems);
+}
+}  // namespace
 
 size_t jacobi_params_elems(int64_t n) { return (size_t)8 * (n / 2 + 2) + 8 + n; }
 
@@ -663,59 +804,133 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   // --- FP32 sweeps on the converted matrix
   const dim3 g2((unsigned)cdiv(n, 128), (unsigned)n, 1);
   init32_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.G32a, wk.Z32); count_launch();
-  int sw32 = 0, sw64 = 0;
-  bool conv32 = false, conv = false, in_g1 = false;
+  int sw32 = 0;
+  bool conv32 = false, in_g1 = false;
   RC_(run_coop<float>(s, n, wk.G32a, wk.G32b, wk.Z32, reinterpret_cast<float*>(wk.params), wk.red,
                       30, 4e-6, 1e-4, &sw32, &conv32, &in_g1));
-  // --- FP64: Z = orthonormalised FP32 eigenvectors, G' = Z^H G Z
+  // --- FP64: refine the FP32 eigenvectors (Ogita-Aishima steps, FP64 GEMMs)
   promote_kernel<<<g2, 128, 0, s>>>(n, wk.Z32, wk.Zw); count_launch();
-  if (zgram(s, n, n, n, wk.Zw, n, wk.Zw, n, wk.T, n, true, wk.gram_ws, wk.gram_ws_elems) !=
+  const unsigned gb = (unsigned)cdiv(n, 256);
+  const int64_t nb = (int64_t)gb * n;  // partial slots (2 doubles each) of the E kernel
+  double* lam = wk.params;             // n eigenvalue estimates (params is free here)
+  double* out2 = wk.red + 2 * kCoopMaxGrid + 12;
+  double2* X = wk.Zw;
+  double2* Xn = wk.Zw2;
+  // |G| scale for the cluster test: largest column-block norm
+  frob2_kernel<<<dim3(gb, (unsigned)n, 1), 256, 0, s>>>(n, G, ldg, reinterpret_cast<double*>(wk.T));
+  count_launch();
+  max2_kernel<<<1, 256, 0, s>>>(nb, reinterpret_cast<double*>(wk.T), out2); count_launch();
+  if (cudaMemcpyAsync(wk.host_red, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
-      potrf_upper(s, n, wk.T, n, wk.dinv, wk.info) != cudaSuccess ||
-      trsm_right_upper(s, n, n, wk.Zw, n, wk.T, n, wk.dinv, wk.info) != cudaSuccess)
-    return CHASE_ERR_CUDA;
-  int hinfo = 0;
-  if (cudaMemcpyAsync(&hinfo, wk.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return CHASE_ERR_CUDA;
-  double2* Gcur = wk.Gw;
-  if (hinfo != 0) {
-    // the FP32 basis is unusable (should not happen): plain FP64 Jacobi from G
-    init_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.Gw, wk.Zw); count_launch();
-  } else {
+  const double gscale = wk.host_red[0] * std::sqrt((double)n);  // >= ||G||_2 / sqrt(n)-ish bound
+  int refine = 0;
+  double emax = 1.0, cmax = 0.0;
+  for (; refine < 4; ++refine) {
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = wk.T;
     ep.ldy = n;
-    if (zgemm_nn(s, n, n, n, G, ldg, wk.Zw, n, ep) != cudaSuccess ||                  // T = G Z
-        zgram(s, n, n, n, wk.Zw, n, wk.T, n, wk.Gw, n, false, wk.gram_ws, wk.gram_ws_elems) !=
-            cudaSuccess ||                                                            // Z^H G Z
+    if (heev_nn(s, wk, n, G, ldg, X, ep) != cudaSuccess ||         // T = G X
+        heev_cn(s, wk, n, X, wk.T, wk.Gw, false) != cudaSuccess ||   // S = X^H T
+        heev_cn(s, wk, n, X, X, wk.Gw2, true) != cudaSuccess)        // X^H X
+      return CHASE_ERR_CUDA;
+    oa_lambda_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, wk.Gw2, lam); count_launch();
+    // E into T (T is free once S is formed)
+    oa_e_kernel<<<dim3(gb, (unsigned)n, 1), 256, 0, s>>>(n, wk.Gw, wk.Gw2, lam, wk.T,
+                                                        reinterpret_cast<double*>(wk.G32a));
+    count_launch();
+    max2_kernel<<<1, 256, 0, s>>>(nb, reinterpret_cast<double*>(wk.G32a), out2); count_launch();
+    // Xn = X + X E
+    if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      return CHASE_ERR_CUDA;
+    Epilogue eu{};
+    eu.mode = EPI_FILTER;
+    eu.alpha = 1.0;
+    eu.beta = 1.0;
+    eu.gamma = 0.0;
+    eu.X = Xn;
+    eu.ldx = n;
+    eu.Y = Xn;
+    eu.ldy = n;
+    if (heev_nn(s, wk, n, X, n, wk.T, eu) != cudaSuccess) return CHASE_ERR_CUDA;
+    std::swap(X, Xn);
+    if (cudaMemcpyAsync(wk.host_red, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CHASE_ERR_CUDA;
+    emax = wk.host_red[0];
+    cmax = wk.host_red[1];
+    // the applied correction was ~emax; the error left is ~emax^2
+    if (emax <= 1e-8) {
+      ++refine;
+      break;
+    }
+  }
+  {
+    // the corrections of close pairs carry rounding of order u / gap; one more
+    // orthogonalisation step brings X^H X back to I at working precision
+    if (heev_cn(s, wk, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_ERR_CUDA;
+    half_residual_kernel<<<g2, 128, 0, s>>>(n, wk.Gw2, wk.T); count_launch();
+    if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      return CHASE_ERR_CUDA;
+    Epilogue eo{};
+    eo.mode = EPI_FILTER;
+    eo.alpha = 1.0;
+    eo.beta = 1.0;
+    eo.gamma = 0.0;
+    eo.X = Xn;
+    eo.ldx = n;
+    eo.Y = Xn;
+    eo.ldy = n;
+    if (heev_nn(s, wk, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_ERR_CUDA;
+    std::swap(X, Xn);
+  }
+  int sw64 = 0;
+  bool conv = emax <= 1e-8;
+  double2* Zfinal = X;
+  double* wsrc = lam;
+  if (!conv || cmax > 1e-14 * gscale) {
+    // pairs the refinement could not separate (or no convergence): FP64 Jacobi
+    // sweeps on G' = X^H G X finish them; eigenvectors X Z'
+    Epilogue ep{};
+    ep.mode = EPI_STORE;
+    ep.Y = wk.T;
+    ep.ldy = n;
+    if (zgemm_nn(s, n, n, n, G, ldg, X, n, ep) != cudaSuccess ||
+        zgram(s, n, n, n, X, n, wk.T, n, wk.Gw, n, false, wk.gram_ws, wk.gram_ws_elems) !=
+            cudaSuccess ||
         hermitian_part(s, n, wk.Gw, n) != cudaSuccess)
       return CHASE_ERR_CUDA;
-  }
-  double2* Zrot = hinfo != 0 ? wk.Zw : wk.Zw2;
-  if (hinfo == 0) {
-    identity_kernel<<<g2, 128, 0, s>>>(n, wk.Zw2); count_launch();
-  }
-  RC_(run_coop<double>(s, n, wk.Gw, wk.Gw2, Zrot, wk.params, wk.red, kMaxSweeps, 1e-15, 1e-12,
-                       &sw64, &conv, &in_g1));
-  if (in_g1) Gcur = wk.Gw2;
-  double2* Zfinal = Zrot;
-  if (hinfo == 0) {  // eigenvectors of G: Z (FP32 stage) times the FP64 rotations
-    Epilogue ep{};
-    ep.mode = EPI_STORE;
-    ep.Y = wk.T;
-    ep.ldy = n;
-    if (zgemm_nn(s, n, n, n, wk.Zw, n, wk.Zw2, n, ep) != cudaSuccess) return CHASE_ERR_CUDA;
+    double2* Zrot = Xn;  // the buffer X does not use
+    identity_kernel<<<g2, 128, 0, s>>>(n, Zrot); count_launch();
+    bool in_g1_64 = false;
+    RC_(run_coop<double>(s, n, wk.Gw, wk.Gw2, Zrot, wk.params, wk.red, kMaxSweeps, 1e-15, 1e-12,
+                         &sw64, &conv, &in_g1_64));
+    double2* Gcur = in_g1_64 ? wk.Gw2 : wk.Gw;
+    Epilogue ez{};
+    ez.mode = EPI_STORE;
+    ez.Y = wk.T;
+    ez.ldy = n;
+    if (zgemm_nn(s, n, n, n, X, n, Zrot, n, ez) != cudaSuccess) return CHASE_ERR_CUDA;
     Zfinal = wk.T;
+    int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
+    rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, Gcur, w, rank); count_launch();
+    permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(
+        n, Zfinal, rank, Z, ldz); count_launch();
+    wsrc = nullptr;
   }
-  const int sweep = sw32 + sw64;
-  int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
-  rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, Gcur, w, rank); count_launch();
-  permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, Zfinal, rank,
-                                                                                    Z, ldz); count_launch();
+  if (wsrc) {
+    int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
+    rank_vec_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, lam, w, rank); count_launch();
+    permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(
+        n, Zfinal, rank, Z, ldz); count_launch();
+  }
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
-  if (sweeps_out) *sweeps_out = sweep;
+  if (sweeps_out) *sweeps_out = sw32 + sw64 + refine;
   return conv ? CHASE_OK : CHASE_ERR_HEEV_NOCONV;
 }
 

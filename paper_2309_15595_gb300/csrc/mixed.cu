@@ -176,8 +176,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TM;
-  const int64_t tile = (P.j0 >> 7) + blockIdx.y;  // absolute 128-column tile
+  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
+  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, 16, rb, ct);
+  const int64_t m0 = (int64_t)rb * TM;
+  const int64_t tile = (P.j0 >> 7) + ct;          // absolute 128-column tile
   const int nkb = (int)((2 * P.Np) / TK);
 
   if (threadIdx.x == 0) {

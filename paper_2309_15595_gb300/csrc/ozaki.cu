@@ -187,8 +187,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TM;
-  const int64_t tile = P.j0 / CT + blockIdx.y;    // absolute CT-column tile
+  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
+  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, 8, rb, ct);
+  const int64_t m0 = (int64_t)rb * TM;
+  const int64_t tile = P.j0 / CT + ct;            // absolute CT-column tile
   const int nkb = (int)((2 * P.Np) / TK);
   const int nchunks = nkb / CHUNK_KB;
 
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (P.mode == EPI_RESID && go) {
       // per column: sum over this warp's 32 rows, one partial per 32-row tile
       const int64_t nt32 = (P.N + 31) / 32;
-      const int64_t t32 = blockIdx.x * 4 + q;
+      const int64_t t32 = (int64_t)rb * 4 + q;
 #pragma unroll
       for (int jj = 0; jj < HC; ++jj) {
         double v = rsq[jj];

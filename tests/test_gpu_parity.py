@@ -283,3 +283,27 @@ def test_full_size_sampled_parity(lib):
         Q_h = host(Vd)
         rr = O.residuals(A_h, Q_h[:, cols], theta[cols])
         np.testing.assert_allclose(r.cpu().numpy()[cols], rr, rtol=1e-11)
+
+
+# ------------------------------------------------- heev with (near-)degeneracy
+@pytest.mark.parametrize("n", [100, 257])
+def test_rayleigh_ritz_degenerate_clusters(lib, n):
+    # the Jacobi heev refines its FP32 sweeps in FP64; degenerate and nearly
+    # degenerate eigenvalues (which first-order refinement cannot separate)
+    # must still give exact Ritz values, orthonormal vectors and tiny residuals
+    N = 2 * n + 37
+    lam = np.concatenate([np.ones(5), [2.0, 2.0 + 1e-9, 2.0 + 2e-9], 3.0 + 7.0 * np.arange(N - 8) / N])
+    U = np.linalg.qr(complex_normal(n, 81, N * N).reshape(N, N))[0]
+    A = np.asfortranarray((U * lam[None, :]) @ U.conj().T)
+    A = 0.5 * (A + A.conj().T)
+    W = np.linalg.qr(complex_normal(n, 82, n * n).reshape(n, n))[0]
+    Q = np.asfortranarray(U[:, :n] @ W)
+    with lib.Context(lib.default_params(N, n - n // 4, n // 4)) as ctx:
+        Vd = dev(Q, lib)
+        ritz = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.chase_rayleigh_ritz(dev(A, lib), Vd, n, ritz)
+        th = ritz.cpu().numpy()
+        V = host(Vd)
+    assert np.abs(th - lam[:n]).max() <= 1e-12 * 10
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() <= 1e-12
+    assert np.linalg.norm(A @ V - V * th[None, :], axis=0).max() <= 1e-12 * 10
