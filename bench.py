@@ -358,6 +358,7 @@ def run_gpu(args):
     roof = filter_roofline(lib, prec, args.fp64_tensor, ms_filter, N, ne, deg)
     phases = {k: sum(s[k] for s in stats) / len(stats) for k in PHASES}
     phases["heev_sweeps"] = stats[-1]["heev_sweeps"]
+    phases["heev_fp64_sweeps"] = stats[-1]["heev_fp64_sweeps"]
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     line = {
@@ -496,7 +497,8 @@ def run_tts(args):
                   "switch_iter": st["switch_iter"], "max_rel_resid": res,
                   "max_rel_eig_err": err, "phase_ms": {k: st[k] for k in (
                       "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid")},
-                  "heev_sweeps": st["heev_sweeps"], "qr_variants": st["qr_variant_count"],
+                  "heev_sweeps": st["heev_sweeps"], "heev_fp64_sweeps": st["heev_fp64_sweeps"],
+                  "qr_variants": st["qr_variant_count"],
                   "filter_tflops_fp64_equiv": st["filter_flops"] / (st["ms_filter"] * 1e9)}
         print(json.dumps({"mode": m, **out[m]}), file=sys.stderr, flush=True)
     line = {"metric": METRIC, "kind": "time-to-solution", "unit": "s", "higher_is_better": False,

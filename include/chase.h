@@ -102,8 +102,9 @@ typedef struct chase_stats {
   int32_t qr_variant_count[5];  /* index = CHASE_QR_* */
   int32_t switch_iter;    /* iteration at which the filter became FP64 (0: never mixed) */
   int64_t kernel_launches;  /* kernels this library launched during the solve */
-  int32_t heev_sweeps;    /* Jacobi sweeps summed over the solve's Rayleigh-Ritz steps */
-  int32_t reserved2;
+  int32_t heev_sweeps;    /* heev iterations summed over the solve: FP32 Jacobi sweeps, FP64
+                             refinement steps and FP64 Jacobi sweeps */
+  int32_t heev_fp64_sweeps;  /* Jacobi heev: FP64 sweeps run for pairs the refinement could not separate */
   double ms_heev;         /* part of ms_rr spent in the Jacobi eigensolver */
 } chase_stats;
 

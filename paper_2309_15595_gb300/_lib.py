@@ -54,7 +54,7 @@ class ChaseStats(ctypes.Structure):
         ("qr_variant_count", ctypes.c_int32 * 5),
         ("switch_iter", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64),
-        ("heev_sweeps", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("heev_sweeps", ctypes.c_int32), ("heev_fp64_sweeps", ctypes.c_int32),
         ("ms_heev", ctypes.c_double),
     ]
 

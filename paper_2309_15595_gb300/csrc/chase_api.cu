@@ -310,7 +310,9 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
       cudaEventCreate(&h1);
       cudaEventRecord(h0, c->stream);
     }
-    const int rc = jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps);
+    int sweeps64 = 0;
+    const int rc =
+        jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps, &sweeps64);
     if (st) {
       cudaEventRecord(h1, c->stream);
       cudaEventSynchronize(h1);
@@ -318,6 +320,7 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
       cudaEventElapsedTime(&ms, h0, h1);
       st->ms_heev += ms;
       st->heev_sweeps += sweeps;
+      st->heev_fp64_sweeps += sweeps64;
       cudaEventDestroy(h0);
       cudaEventDestroy(h1);
     }

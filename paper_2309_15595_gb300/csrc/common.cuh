@@ -141,7 +141,7 @@ struct JacobiWork {
 size_t jacobi_params_elems(int64_t n);
 size_t jacobi_red_elems();  // doubles of JacobiWork::red
 int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
-                int64_t ldz, JacobiWork& wk, int* sweeps_out);
+                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out = nullptr);
 // Batched small Jacobi (n <= 64) on `batch` column-major n x n matrices with
 // stride n*n; eigenvalues ascending (w: batch x n), eigenvectors Z; *status
 // (device) set to 1 when a sweep cap is hit.

@@ -778,7 +778,7 @@ cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2
 }
 
 int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
-                int64_t ldz, JacobiWork& wk, int* sweeps_out) {
+                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out) {
   if (n <= 0) return CHASE_OK;
   cudaError_t e;
   int* status = reinterpret_cast<int*>(wk.red + 2 * kCoopMaxGrid + 8);
@@ -827,7 +827,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   const double gscale = wk.host_red[0] * std::sqrt((double)n);  // >= ||G||_2 / sqrt(n)-ish bound
   int refine = 0;
   double emax = 1.0, cmax = 0.0;
-  for (; refine < 4; ++refine) {
+  for (; refine < 8; ++refine) {  // 2-4 steps from FP32 accuracy; a slow start gets more
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = wk.T;
@@ -931,6 +931,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   }
   if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
   if (sweeps_out) *sweeps_out = sw32 + sw64 + refine;
+  if (fp64_sweeps_out) *fp64_sweeps_out = sw64;
   return conv ? CHASE_OK : CHASE_ERR_HEEV_NOCONV;
 }
 
