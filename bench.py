@@ -36,6 +36,10 @@ METRIC = "time-to-solution at resid≤1e-10, mixed vs FP64; filter TFLOP/s vs pe
 # six signed 8-bit digits per real operand; the products of digit pairs s + t <= 7
 # are issued (1 + 2 + ... + 6 = 21 BF16 MMAs per real multiply-add)
 OZ_PAIRS = 21.0
+# DRAM bytes (read + write) of one filter launch of ozaki_gemm_kernel at full size,
+# from one ncu capture of the same bench command (profiles/ozaki_gemm_filter_C2like_N8000.md);
+# keyed by (N, nev + nex)
+OZAKI_FILTER_DRAM_BYTES = {}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
@@ -261,9 +265,12 @@ def filter_roofline(lib, prec, tensor, ms_filter, N, ne, deg):
     if prec == lib.CHASE_FP64 and tensor:
         # issued tensor work: OZ_PAIRS BF16 digit-pair products per real MAC of the planar GEMM
         peak = measured_bf16_peak()
+        traffic = OZAKI_FILTER_DRAM_BYTES.get((N, ne))
         return {"kernel": "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)",
                 "bound": "tensor", "achieved": OZ_PAIRS * achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": OZ_PAIRS * achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": OZ_PAIRS * achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
+                                "dram__bytes_write.sum, one capture)" if traffic else None,
                 "launches_per_step": deg, "flops_per_launch": OZ_PAIRS * flops_launch,
                 "fp64_equivalent_tflops": achieved,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}

@@ -742,14 +742,14 @@ size_t jacobi_red_elems() { return (size_t)2 * kCoopMaxGrid + 16; }
 namespace {
 // refinement products: P = A B (n x n) or P = X^H Y, on the tensor cores when
 // the context supplied a product, else with the CUDA-core kernels
-cudaError_t heev_nn(cudaStream_t s, const JacobiWork& wk, int64_t n, const double2* A,
+cudaError_t heev_nn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, const double2* A,
                     int64_t lda, const double2* B, const Epilogue& ep) {
-  if (wk.gemm) return wk.gemm(wk.gemm_ctx, n, n, A, lda, false, n, B, n, ep);
+  if (tc && wk.gemm) return wk.gemm(wk.gemm_ctx, n, n, A, lda, false, n, B, n, ep);
   return zgemm_nn(s, n, n, n, A, lda, B, n, ep);
 }
-cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, int64_t n, const double2* X,
+cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, const double2* X,
                     const double2* Y, double2* P, bool hermitian) {
-  if (wk.gemm) {
+  if (tc && wk.gemm) {
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = P;
@@ -827,14 +827,20 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   const double gscale = wk.host_red[0] * std::sqrt((double)n);  // >= ||G||_2 / sqrt(n)-ish bound
   int refine = 0;
   double emax = 1.0, cmax = 0.0;
+  // The digit-sliced tensor-core products (when the context supplies them) carry
+  // an error of about sqrt(n) 2^-47 of ||G||, far above what the Ritz values
+  // need: they serve the first, coarse steps only; once the corrections fall
+  // below 1e-6 the products are the CUDA-core FP64 ones, and so are the final
+  // step and the orthogonalisation.
+  bool tc = wk.gemm != nullptr;
   for (; refine < 8; ++refine) {  // 2-4 steps from FP32 accuracy; a slow start gets more
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = wk.T;
     ep.ldy = n;
-    if (heev_nn(s, wk, n, G, ldg, X, ep) != cudaSuccess ||         // T = G X
-        heev_cn(s, wk, n, X, wk.T, wk.Gw, false) != cudaSuccess ||   // S = X^H T
-        heev_cn(s, wk, n, X, X, wk.Gw2, true) != cudaSuccess)        // X^H X
+    if (heev_nn(s, wk, tc, n, G, ldg, X, ep) != cudaSuccess ||         // T = G X
+        heev_cn(s, wk, tc, n, X, wk.T, wk.Gw, false) != cudaSuccess ||   // S = X^H T
+        heev_cn(s, wk, tc, n, X, X, wk.Gw2, true) != cudaSuccess)        // X^H X
       return CHASE_ERR_CUDA;
     oa_lambda_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, wk.Gw2, lam); count_launch();
     // E into T (T is free once S is formed)
@@ -855,7 +861,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     eu.ldx = n;
     eu.Y = Xn;
     eu.ldy = n;
-    if (heev_nn(s, wk, n, X, n, wk.T, eu) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_nn(s, wk, tc, n, X, n, wk.T, eu) != cudaSuccess) return CHASE_ERR_CUDA;
     std::swap(X, Xn);
     if (cudaMemcpyAsync(wk.host_red, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
@@ -863,16 +869,18 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
       return CHASE_ERR_CUDA;
     emax = wk.host_red[0];
     cmax = wk.host_red[1];
-    // the applied correction was ~emax; the error left is ~emax^2
-    if (emax <= 1e-8) {
+    // the applied correction was ~emax; the error left is ~emax^2 (plus the
+    // products' own error, hence the last step on the CUDA cores)
+    if (emax <= 1e-8 && !tc) {
       ++refine;
       break;
     }
+    if (emax <= 1e-6) tc = false;
   }
   {
     // the corrections of close pairs carry rounding of order u / gap; one more
     // orthogonalisation step brings X^H X back to I at working precision
-    if (heev_cn(s, wk, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_cn(s, wk, false, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_ERR_CUDA;
     half_residual_kernel<<<g2, 128, 0, s>>>(n, wk.Gw2, wk.T); count_launch();
     if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
@@ -886,11 +894,11 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     eo.ldx = n;
     eo.Y = Xn;
     eo.ldy = n;
-    if (heev_nn(s, wk, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_nn(s, wk, false, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_ERR_CUDA;
     std::swap(X, Xn);
   }
   int sw64 = 0;
-  bool conv = emax <= 1e-8;
+  bool conv = emax <= 1e-8 && !tc;
   double2* Zfinal = X;
   double* wsrc = lam;
   if (!conv || cmax > 1e-14 * gscale) {
