@@ -39,7 +39,7 @@ OZ_PAIRS = 21.0
 # DRAM bytes (read + write) of one filter launch of ozaki_gemm_kernel at full size,
 # from one ncu capture of the same bench command (profiles/ozaki_gemm_filter_C2like_N8000.md);
 # keyed by (N, nev + nex)
-OZAKI_FILTER_DRAM_BYTES = {}
+OZAKI_FILTER_DRAM_BYTES = {(20000, 1300): 108.94e9 + 0.452e9}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 

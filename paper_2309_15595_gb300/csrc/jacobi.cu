@@ -816,7 +816,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   double* out2 = wk.red + 2 * kCoopMaxGrid + 12;
   double2* X = wk.Zw;
   double2* Xn = wk.Zw2;
-  // |G| scale for the cluster test: largest column-block norm
+  // scale of G for the cluster test
   frob2_kernel<<<dim3(gb, (unsigned)n, 1), 256, 0, s>>>(n, G, ldg, reinterpret_cast<double*>(wk.T));
   count_launch();
   max2_kernel<<<1, 256, 0, s>>>(nb, reinterpret_cast<double*>(wk.T), out2); count_launch();
@@ -824,7 +824,9 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return CHASE_ERR_CUDA;
-  const double gscale = wk.host_red[0] * std::sqrt((double)n);  // >= ||G||_2 / sqrt(n)-ish bound
+  // sqrt(n) times the largest norm of a 256-row column segment: within a factor
+  // sqrt(n) of ||G||_2 either way, enough for the 1e-14 cluster test below
+  const double gscale = wk.host_red[0] * std::sqrt((double)n);
   int refine = 0;
   double emax = 1.0, cmax = 0.0;
   // The digit-sliced tensor-core products (when the context supplies them) carry

@@ -46,7 +46,7 @@ namespace chase {
 namespace {
 
 constexpr int OS = 6;                    // digits per operand
-static_assert(OS == 6, "the epilogue keeps levels 2-5 exact and reads levels 6-7 once");
+static_assert(OS == 6, "the epilogue keeps levels 2-5 exact and levels 6-7 in FP32");
 constexpr int TM = 128, TN = 64, TK = 32, STAGES = 3;
 constexpr int CHUNK_KB = 8;              // K blocks per exact chunk (256 values)
 constexpr int A_TILE = TM * TK * 2;      // 8 KB per digit
@@ -273,10 +273,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
               for (int sa = 1; sa < L; ++sa) {
                 const int tb = L - sa;
-                // levels 2-5 restart every chunk (exact integers below 2^24);
-                // levels 6-7 accumulate in FP32 over the whole K range
-                const uint32_t acc =
-                    (kc == 0 && kk == 0 && sa == 1 && (L <= 5 || c == 0)) ? 0u : 1u;
+                // every level restarts each 256-long chunk (levels 2-5 then stay
+                // exact integers below 2^24)
+                const uint32_t acc = (kc == 0 && kk == 0 && sa == 1) ? 0u : 1u;
                 umma_bf16(tmem + (uint32_t)((L - 2) * TN),
                           sdesc_sw64(st + (sa - 1) * A_TILE + off),
                           sdesc_sw64(st + OS * A_TILE + (tb - 1) * B_TILE + off), acc);
@@ -299,8 +298,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t row = m0 + q * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
     long long acc[2 * HC];                    // re[0..16), im[16..32): levels 2-5, weight 2^-40
+    float acc67[2 * HC];                      // levels 6-7, weight 2^-48
 #pragma unroll
-    for (int j = 0; j < 2 * HC; ++j) acc[j] = 0;
+    for (int j = 0; j < 2 * HC; ++j) {
+      acc[j] = 0;
+      acc67[j] = 0.f;
+    }
     bool go = true;
     for (int c = 0; c < nchunks; ++c) {
       const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), (uint32_t)c & 1u, P.err, 15);
@@ -309,36 +312,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // levels 2..5 are exact integers below 2^24 per chunk: int64 at weight
       // 2^-40 (level L shifted by 8 (5 - L) bits). Levels 6 and 7 (weights
-      // 2^-48, 2^-56, at most 2^-24 of the leading level) stay in TMEM in FP32
-      // across all chunks and are read once after the last one.
+      // 2^-48, 2^-56, at most 2^-24 of the leading level) go to FP32 registers
+      // per chunk. (Accumulating them in TMEM over the whole K range instead
+      // lost accuracy at K = 80000: a Ritz-value floor near 1e-10 ||A||.)
 #pragma unroll
-      for (int L = 2; L <= 5; ++L) {
-        float v[2 * HC];  // real columns, then imaginary: two loads, one wait
-        const uint32_t base = tl + (uint32_t)((L - 2) * TN + h * HC);
-        tmem_ld16(base, v);
-        tmem_ld16(base + CT, v + HC);
-        tmem_wait_ld();
-        const int sh = 8 * (5 - L);
+      for (int L = 2; L <= OS + 1; ++L) {
 #pragma unroll
-        for (int j = 0; j < 2 * HC; ++j) acc[j] += (long long)__float2int_rn(v[j]) << sh;
+        for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
+          float v[HC];
+          tmem_ld16(tl + (uint32_t)((L - 2) * TN + part * CT + h * HC), v);
+          tmem_wait_ld();
+          if (L <= 5) {
+            const int sh = 8 * (5 - L);
+#pragma unroll
+            for (int j = 0; j < HC; ++j)
+              acc[part * HC + j] += (long long)__float2int_rn(v[j]) << sh;
+          } else {
+            const float w = L == 6 ? 1.0f : 0.00390625f;
+#pragma unroll
+            for (int j = 0; j < HC; ++j) acc67[part * HC + j] = fmaf(w, v[j], acc67[part * HC + j]);
+          }
+        }
       }
-
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars[2 * STAGES + 1]));
-    }
-    // levels 6-7, weight 2^-48 and 2^-56: read once after the last chunk
-    float acc67[2 * HC];
-    if (go) {
-      float v6[2 * HC], v7[2 * HC];
-      const uint32_t b6 = tl + (uint32_t)(4 * TN + h * HC), b7 = tl + (uint32_t)(5 * TN + h * HC);
-      tmem_ld16(b6, v6);
-      tmem_ld16(b6 + CT, v6 + HC);
-      tmem_ld16(b7, v7);
-      tmem_ld16(b7 + CT, v7 + HC);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 2 * HC; ++j) acc67[j] = fmaf(0.00390625f, v7[j], v6[j]);
     }
     // ------------------------------------------------ FP64 result + update
     double rsq[HC];

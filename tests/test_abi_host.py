@@ -77,3 +77,22 @@ def test_degree_opt_matches_oracle_bitwise(pkg):
         got = pkg.chase_degree_opt(resid, ritz, c, e, tol_abs, 36, 2)
         ref = O.degree_opt(resid, ritz, c, e, tol_abs, 36, 2)
         assert np.array_equal(got, ref)
+
+
+def test_new_entry_points_reject_invalid_arguments_without_gpu(pkg):
+    # argument checks run before any CUDA call: null contexts and pointers,
+    # negative counts are refused; an empty batch is a no-op
+    L = pkg.LIB
+    INVALID = 1
+    status = (ctypes.c_int32 * 1)()
+    assert L.chase_solve_batch(-1, None, None, None, None, None, None, None, None, None, None,
+                               status, 0) == INVALID
+    assert L.chase_solve_batch(0, None, None, None, None, None, None, None, None, None, None,
+                               None, 0) == 0
+    assert L.chase_solve_batch(1, None, None, None, None, None, None, None, None, None, None,
+                               status, 0) == INVALID
+    assert L.chase_filter_vjp(None, None, 1, None, 1, 1, 2, 1.0, 1.0, -1.0, None, 1, None, 1,
+                              None, 1, 0) == INVALID
+    it = ctypes.c_int32(0)
+    assert L.chase_eig_vjp(None, None, 1, None, 1, None, 1, 1, None, None, 1, None, 1, 1e-10,
+                           100, ctypes.byref(it)) == INVALID
