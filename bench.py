@@ -36,10 +36,11 @@ METRIC = "time-to-solution at resid≤1e-10, mixed vs FP64; filter TFLOP/s vs pe
 # six signed 8-bit digits per real operand; the products of digit pairs s + t <= 7
 # are issued (1 + 2 + ... + 6 = 21 BF16 MMAs per real multiply-add)
 OZ_PAIRS = 21.0
-# DRAM bytes (read + write) of one filter launch of ozaki_gemm_kernel at full size,
-# from one ncu capture of the same bench command (profiles/ozaki_gemm_filter_C2like_N8000.md);
-# keyed by (N, nev + nex)
-OZAKI_FILTER_DRAM_BYTES = {(20000, 1300): 108.94e9 + 0.452e9}
+# DRAM bytes (read + write) of one filter launch of ozaki_gemm_kernel at full size, from
+# one ncu capture of the same bench command, keyed by (N, nev + nex). Left empty while the
+# kernel differs from the captured version (the last capture, 109.4 GB per launch at
+# N = 20000, preceded the change of its level-6/7 accumulation).
+OZAKI_FILTER_DRAM_BYTES = {}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
