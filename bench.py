@@ -438,10 +438,12 @@ def run_gpu(args):
         if prec == lib.CHASE_FP64:
             variants.append(("variant_mixed", lib.CHASE_MIXED_BF16X3, args.fp64_tensor,
                              args.warmup))
-            # the CUDA-core FP64 step takes over a minute at this size: one warm-up
-            variants.append(("variant_fp64_dfma" if args.fp64_tensor else "variant_fp64_tensor",
-                             lib.CHASE_FP64, 1 - args.fp64_tensor,
-                             1 if args.fp64_tensor else args.warmup))
+            # the CUDA-core FP64 step takes over a minute at this size: one warm-up,
+            # and only in single-GPU runs (replica runs keep their timed work short)
+            if world == 1 or not args.fp64_tensor:
+                variants.append(("variant_fp64_dfma" if args.fp64_tensor
+                                 else "variant_fp64_tensor", lib.CHASE_FP64,
+                                 1 - args.fp64_tensor, 1 if args.fp64_tensor else args.warmup))
         for key, vprec, vt, vw in variants:
             vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=vprec,
                                       fp64_tensor=vt)
