@@ -625,6 +625,26 @@ def run_grad(args):
     return 0
 
 
+def shard_problems(costs, world):
+    """Longest-processing-time assignment of independent problems to `world`
+    ranks: problems in descending cost (ties by index), each to the rank with the
+    least cost so far (ties: lowest rank). Deterministic, so every rank computes
+    the same shards. Returns one sorted index list per rank."""
+    load = [0.0] * world
+    shards = [[] for _ in range(world)]
+    for k in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda j: (load[j], j))
+        shards[r].append(k)
+        load[r] += costs[k]
+    return [sorted(x) for x in shards]
+
+
+def batch_sizes(nprob):
+    from synth import uniform01
+
+    return [int(256 + (4096 - 256) * u) for u in uniform01(5, 1, nprob)]
+
+
 def run_batch(args):
     """Batched warm-start sequence (C5): --batch-problems problems with N drawn
     uniformly from [256, 4096], nev = ceil(N/20), nex = ceil(N/40), uniform
@@ -632,18 +652,32 @@ def run_batch(args):
     A_{t+1} = A_t + 1e-3 E_t (||E_t||_2 = 1), warm-started from the previous
     Ritz vectors, mixed-precision filter, all problems of a step in one
     chase_solve_batch call. Perturbations are generated outside the timed
-    region; each step's batch call is timed with CUDA events."""
+    region; each step's batch call is timed with CUDA events. Under torchrun
+    the problems are split over the ranks by cost (N^2 (nev + nex)), with no
+    collective on the data path; the time is the slowest rank's."""
     import torch
 
     import paper_2309_15595_gb300 as lib
-    from synth import Problem, complex_normal, uniform01
+    from synth import Problem, complex_normal
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     nprob, nsteps = args.batch_problems, args.batch_steps
-    Ns = [int(256 + (4096 - 256) * u) for u in uniform01(5, 1, nprob)]
-    probs = [Problem(N=N, nev=-(-N // 20), nex=-(-N // 40), spectrum="uniform", lo=0.0,
-                     hi=10.0, reflectors=8, seed=1000 + k) for k, N in enumerate(Ns)]
+    Ns = batch_sizes(nprob)
+    costs = [float(N) ** 2 * (-(-N // 20) - (-N // 40)) for N in Ns]
+    mine = shard_problems(costs, world)[rank]
+    probs = [Problem(N=Ns[k], nev=-(-Ns[k] // 20), nex=-(-Ns[k] // 40), spectrum="uniform",
+                     lo=0.0, hi=10.0, reflectors=8, seed=1000 + k) for k in mine]
     As = [p.matrix_torch(dev) for p in probs]
     streams = [torch.cuda.Stream(dev) for _ in probs]
     ctxs = [lib.Context(lib.default_params(p.N, p.nev, p.nex, precision=lib.CHASE_MIXED_BF16X3,
@@ -654,7 +688,7 @@ def run_batch(args):
     rs = [torch.zeros_like(r) for r in rz]
 
     def perturb(t):
-        for k, (p, A) in enumerate(zip(probs, As)):
+        for k, p, A in zip(mine, probs, As):
             Z = torch.from_numpy(complex_normal(2000 + k, 100 + t, p.N * p.N)
                                  .reshape(p.N, p.N)).to(dev)
             E = 0.5 * (Z + Z.conj().T)
@@ -687,16 +721,24 @@ def run_batch(args):
     clk = clocks.stop()
     for cx in ctxs:
         cx.close()
-    total = sum(step_ms) / 1000.0
+    # whole job: all problems, the slowest rank's time (no collective on the data path)
+    _, total_ms, world = aggregate_over_ranks(sum(step_ms), 1, dist, dev)
+    total = total_ms / 1000.0
     line = {"metric": METRIC, "kind": "batched warm-start sequence",
             "value": nprob * nsteps / total, "unit": "solves/s", "higher_is_better": True,
+            "n_gpus": world, "scaling": "strong",
             "config": {"workload": f"C5: {nprob} problems, N uniform in [256, 4096], nev = "
                                    f"ceil(N/20), nex = ceil(N/40), {nsteps} steps A += 1e-3 E, "
                                    "warm starts, mixed filter",
-                       "threads": args.batch_threads, "fp64_tensor": args.fp64_tensor},
-            "total_s": total, "step_ms": step_ms, "iterations_per_step": iters,
-            "matvecs_per_step": mvs, "clocks": clk, "data": "synthetic"}
-    print(json.dumps(line))
+                       "threads": args.batch_threads, "fp64_tensor": args.fp64_tensor,
+                       "parallelism": "problems split over ranks by cost" if world > 1
+                                      else "single GPU"},
+            "total_s": total, "step_ms_rank0": step_ms, "iterations_per_step_rank0": iters,
+            "matvecs_per_step_rank0": mvs, "clocks": clk, "data": "synthetic"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
