@@ -1,17 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the single-GPU ChASE hot path.
 
-Workload (default ``--config C2``): complex Hermitian A with N = 20000,
-nev = 1000, nex = 300, geometric spectrum 1e-4 .. 1, A = H D H^H with 16
-Householder reflectors, FP64. One step is one pass of the whole hot path
-through the C ABI (``chase_solve`` with max_iter = 1): Lanczos bounds, then one
-ChASE iteration (filter of all 1300 vectors at the initial degree 20, CondEst,
-1D-CAQR, restore, Rayleigh-Ritz with Jacobi, residuals, locking and the degree
-update). This is the paper's own unit of measurement for its weak-scaling runs
-(one iteration at fixed nev/nex, Section 4.5).
+Headline workload (default ``--config C3``): complex Hermitian A with
+N = 40000, nev = 2250, nex = 750, the lowest 3000 eigenvalues in clusters of
+four (spacing 1e-3) in [-2, 0), the rest uniform in [0, 50], A = H D H^H with
+16 Householder reflectors (25.6 GB). Precision mode "mixed": the filter runs in
+split-BF16 x3 on the tensor cores while residuals are large, every other step
+(and the filter afterwards) in FP64 with the products on the tensor cores
+(exact digit slicing).
 
-Printed: one JSON line. ``value`` = ChASE iterations per second over the whole
-job (N replicas for --gpus N; the solve does not shard, see the design notes).
+One step is one pass of the whole hot path through the C ABI (``chase_solve``
+with max_iter = 1): Lanczos bounds, then one ChASE iteration (filter of all
+3000 vectors at the initial degree 20, CondEst, 1D-CAQR, restore,
+Rayleigh-Ritz with the Jacobi heev, residuals, locking and the degree update).
+This is the paper's own unit for its weak-scaling runs (one iteration at fixed
+nev, nex; Section 4.5). ``value`` = ChASE iterations per second over the whole
+job (N replicas for --gpus N; a single solve does not shard).
+
+The same JSON line carries, when the wall-clock budget allows (single GPU
+only), one time-to-solution solve (resid <= 1e-10 ||A||) in the mixed mode and
+one in the plain FP64 mode on the same code, each checked against the exactly
+known spectrum and by recomputing sampled residuals with torch. Legs that do
+not fit the budget are skipped and named in the line; the line is always
+printed (also on SIGTERM).
+
 ``--impl reference`` times the CPU FP64 oracle on a bounded sample of the same
 workload instead.
 """
@@ -20,6 +32,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import signal
 import statistics
 import subprocess
 import sys
@@ -28,49 +41,61 @@ import time
 
 import numpy as np
 
+T_START = time.time()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-solution at resid≤1e-10, mixed vs FP64; filter TFLOP/s vs peak"
-# FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz (max SM clock)
 # six signed 8-bit digits per real operand; the products of digit pairs s + t <= 7
 # are issued (1 + 2 + ... + 6 = 21 BF16 MMAs per real multiply-add)
 OZ_PAIRS = 21.0
-# DRAM bytes (read + write) of one filter launch of ozaki_gemm_kernel at full size, from
-# one ncu capture of the same bench command, keyed by (N, nev + nex). Left empty while the
-# kernel differs from the captured version (the last capture, 109.4 GB per launch at
-# N = 20000, preceded the change of its level-6/7 accumulation).
-OZAKI_FILTER_DRAM_BYTES = {}
+# DRAM bytes (read + write) of one filter launch at full size, from ncu captures of the
+# current kernels (see profiles/), keyed by (kernel, N, nev + nex). Empty entries: the
+# kernel changed after the last capture.
+FILTER_DRAM_BYTES = {}
+# FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
-def measured_bf16_peak():
+def measured_peak(key):
+    """bf16 tensor peak from MEASURED_PEAKS.json: `bf16_tflops_sustained` for
+    kernels timed inside a seconds-long step, `bf16_tflops` for a burst."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
+            return float(json.load(f)[key]), "MEASURED_PEAKS.json " + key + ", of measured"
     except Exception:
-        return 1900.0  # profiling-recipe fallback (bf16 burst)
+        return (1700.0 if key.endswith("sustained") else 1900.0), "profiling-recipe fallback, of fallback"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="C2")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--config", default="C3")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--fp64-tensor", type=int, default=1, choices=[0, 1],
                     help="1: FP64 N x N products on the tensor cores (exact digit slicing)")
     ap.add_argument("--N", type=int, default=0, help="override the workload's order (profiling)")
     ap.add_argument("--nev", type=int, default=0)
     ap.add_argument("--nex", type=int, default=-1)
     ap.add_argument("--tts", default="",
-                    help="comma list of modes (fp64, fp64t, mixed, mixedt) for full solves to "
-                         "resid <= tol instead of the per-iteration step")
-    ap.add_argument("--max-iter", type=int, default=100)
+                    help="standalone mode: comma list of modes (fp64, fp64t, mixed, mixedt) "
+                         "for full solves to resid <= tol instead of the per-iteration step")
+    ap.add_argument("--tts-legs", default="mixedt,fp64t",
+                    help="time-to-solution solves carried in the headline line (single GPU, "
+                         "within the budget); empty to skip")
+    ap.add_argument("--budget-s", type=float, default=1380.0,
+                    help="wall-clock seconds from process start after which optional legs "
+                         "(time-to-solution solves, variants) are skipped")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="steps of the end-to-end (host buffers) measurement")
+    ap.add_argument("--max-iter", type=int, default=30)
+    ap.add_argument("--dfma-step", action="store_true",
+                    help="also time one step with the CUDA-core FP64 (DFMA) products")
     ap.add_argument("--no-variant", action="store_true",
-                    help="skip the other precision modes measured beside the headline")
+                    help="skip the step variant in the other precision mode")
     ap.add_argument("--grad", action="store_true",
                     help="differentiation workload (C4): gradient timing and checks")
     ap.add_argument("--grad-fd", type=int, default=2,
@@ -85,10 +110,14 @@ def parse():
     return ap.parse_args()
 
 
+def elapsed():
+    return time.time() - T_START
+
+
 def workload_desc(p, deg):
     return (f"{p.spectrum} spectrum, N={p.N}, nev={p.nev}, nex={p.nex}, {p.reflectors} Householder "
             f"reflectors; step = Lanczos bounds + one ChASE iteration (filter degree {deg} on "
-            f"{p.ne} vectors, CondEst, CAQR, Rayleigh-Ritz, residuals, locking)")
+            f"{p.ne} vectors, CondEst, CAQR, Rayleigh-Ritz with Jacobi heev, residuals, locking)")
 
 
 # ------------------------------------------------------------------ clocks
@@ -160,39 +189,52 @@ def aggregate_over_ranks(ms_local, steps, dist=None, device=None):
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(A, V0, p, deg, ncols=128):
-    """Times the oracle on a bounded sample of one ChASE iteration at full N and
-    extrapolates to the whole iteration: the filter and residual HEMMs on
-    ``ncols`` of the vectors (scaled by columns x degrees), the full-size CAQR
-    and the full-size small eigenproblem. Returns (seconds per iteration,
-    sample description, measured seconds)."""
+def iteration_flops(N, ne, deg):
+    """Flops of one ChASE iteration with all ne vectors active (complex
+    multiply-add = 8 flop): filter 8 N^2 ne deg, two HEMMs for RR and residuals
+    16 N^2 ne, CholeskyQR2 (two Gram + two triangular solves) 4 x 4 N ne^2, the
+    RR Gram and back-transform 2 x 8 N ne^2, a dense Hermitian eigensolver
+    ~ 9 (4/3) ne^3 x 4 (complex)."""
+    return (8.0 * N * N * ne * deg + 16.0 * N * N * ne + 16.0 * N * ne * ne
+            + 16.0 * N * ne * ne + 48.0 * ne ** 3)
+
+
+def oracle_sample(A, V0, p, deg, ncols=16, nq=192, nrr=384):
+    """Times the oracle, as it stands, on a bounded sample of one ChASE
+    iteration at the workload's full N: the filter (degree 2) and the residuals
+    on ``ncols`` of the vectors, CAQR (CholeskyQR2) of an N x ``nq`` slice of the
+    start block and the small eigenproblem at order ``nrr``. Returns (measured
+    seconds, fraction of one iteration's flops the sample did, extrapolated
+    seconds of a whole iteration, description)."""
     from oracle import chase_oracle as O
 
-    ne = p.ne
+    N, ne = p.N, p.ne
     lam = p.eigenvalues()
     b_sup = lam[-1] * 1.01
     c, e, mu1 = (b_sup + lam[ne - 1]) / 2, (b_sup - lam[ne - 1]) / 2, lam[0]
-    ncols = min(ncols, ne)
+    ncols, nq, nrr = min(ncols, ne), min(nq, ne), min(nrr, ne)
     Vs = np.asfortranarray(V0[:, :ncols])
-    ds = 4
+    ds = 2
     t0 = time.perf_counter()
     Y = O.chebyshev_filter(A, Vs, np.full(ncols, ds), c, e, mu1)
     t1 = time.perf_counter()
     O.residuals(A, Y, np.linspace(lam[0], lam[ne], ncols))
     t2 = time.perf_counter()
-    O.caqr(V0, 1e4)
+    O.caqr(np.asfortranarray(V0[:, :nq]), 1e4)
     t3 = time.perf_counter()
-    G = V0[:ne, :ne] + V0[:ne, :ne].conj().T
-    np.linalg.eigh(G)
+    G = V0[:nrr, :nrr] + V0[:nrr, :nrr].conj().T
+    O.rayleigh_ritz(G, np.eye(nrr, dtype=np.complex128))
     t4 = time.perf_counter()
-    per_colmv = (t1 - t0) / (ncols * ds)
-    per_col_resid = (t2 - t1) / ncols
-    t_iter = per_colmv * ne * deg + 2 * per_col_resid * ne + (t3 - t2) + (t4 - t3)
-    desc = (f"oracle at full N={p.N}: filter degree {ds} on {ncols} of {ne} vectors, residuals of "
-            f"{ncols} vectors, CAQR (CholeskyQR2) of the full {p.N}x{ne} block, eigh of a "
-            f"{ne}x{ne} matrix; HEMM parts scaled to {ne} vectors x degree {deg} (+2 HEMMs for RR "
-            f"and residuals)")
-    return t_iter, desc, t4 - t0
+    done = (8.0 * N * N * ncols * ds + 8.0 * N * N * ncols + 16.0 * N * nq * nq
+            + 16.0 * nrr ** 3 + 48.0 * nrr ** 3)
+    frac = done / iteration_flops(N, ne, deg)
+    # per-phase scaling of the measured times to the whole iteration
+    t_iter = ((t1 - t0) / (ncols * ds) * ne * deg + (t2 - t1) / ncols * 2 * ne
+              + (t3 - t2) * (ne / nq) ** 2 + (t4 - t3) * (ne / nrr) ** 3)
+    desc = (f"oracle at full N={N}: filter degree {ds} and residuals on {ncols} of {ne} vectors, "
+            f"CAQR (CholeskyQR2) of an N x {nq} slice, Rayleigh-Ritz eigensolver at order {nrr}; "
+            f"{frac:.2e} of one iteration's flops")
+    return t4 - t0, frac, t_iter, desc
 
 
 def build_matrix_host(p):
@@ -200,7 +242,11 @@ def build_matrix_host(p):
 
     if torch.cuda.is_available():
         Ad = p.matrix_torch("cuda")
-        A = np.asfortranarray(Ad.cpu().numpy())
+        A = np.empty((p.N, p.N), dtype=np.complex128, order="F")
+        # copy in column slabs: a full-size temporary of A would double host memory
+        slab = max(1, (1 << 30) // (16 * p.N))
+        for j in range(0, p.N, slab):
+            A[:, j:j + slab] = Ad[:, j:j + slab].cpu().numpy()
         del Ad
         torch.cuda.empty_cache()
         return A
@@ -218,85 +264,153 @@ def make_problem(args):
     if args.nex >= 0:
         over["nex"] = args.nex
     p = config_problem(args.config, **over)
+    if args.config == "C3" and "N" in over and p.n_low > p.N // 2:
+        p = config_problem(args.config, **over, n_low=p.ne)
     name = args.config if not over else f"{args.config}-like ({', '.join(f'{k}={v}' for k, v in over.items())})"
     return p, name
 
 
 def run_reference(args):
+    """The reference arm: the CPU FP64 oracle (there is no published code), each
+    step a bounded sample of one ChASE iteration of the same workload. value =
+    the fraction of an iteration's flops one sample does / its measured time
+    (iteration-equivalents per second); ms_per_step is the measured time of one
+    sample; the whole-iteration time extrapolated phase by phase is reported
+    beside it, labelled as such."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     p, name = make_problem(args)
     A = build_matrix_host(p)
     V0 = p.start_block()
-    cores = os.cpu_count()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     for _ in range(args.warmup):
         oracle_sample(A, V0, p, 20)
-    times, desc, meas = [], "", 0.0
+    meas, fracs, extrap, desc = [], [], [], ""
     for _ in range(args.steps):
-        t, desc, m = oracle_sample(A, V0, p, 20)
-        times.append(t)
-        meas += m
-    t_iter = sum(times) / len(times)
-    value = 1.0 / t_iter
+        m, f, t_it, desc = oracle_sample(A, V0, p, 20)
+        meas.append(m)
+        fracs.append(f)
+        extrap.append(t_it)
+    ms_step = 1000.0 * sum(meas) / len(meas)
+    value = fracs[0] / (ms_step / 1000.0)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "ChASE iterations/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * t_iter, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{name}: " + workload_desc(p, 20), "N": p.N,
-                   "nev": p.nev, "nex": p.nex, "parallelism": "replicas"},
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "ChASE iterations/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: " + workload_desc(p, 20), "N": p.N, "nev": p.nev,
+                   "nex": p.nex, "parallelism": "host cores"},
+        "sample_fraction_of_iteration": fracs[0],
+        "value_definition": "iteration-equivalents per second: flops of one sample / flops of "
+                            "one iteration, divided by the sample's measured time",
+        "extrapolated_iteration_s": statistics.median(extrap),
+        "extrapolation": "per-phase scaling of the sample's measured times to all vectors, "
+                         "degree 20, the full CAQR and eigensolver orders (not timed)",
         "cpu_baseline": {"value": value, "unit": "ChASE iterations/s", "cores": cores,
-                         "kind": "oracle", "sample": desc + f" (measured {meas:.1f} s)"},
+                         "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "ChASE iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
     return 0
 
 
 # --------------------------------------------------------------------- GPU
 def filter_roofline(lib, prec, tensor, ms_filter, N, ne, deg):
-    """Roofline of the dominant kernel (the filter product, deg launches per
-    step at iteration 1 with all ne vectors active): per-launch time from the
-    library's CUDA events on the launching stream over the timed steps."""
+    """Roofline of the filter product (deg launches per step at iteration 1 with
+    all ne vectors active): per-launch time from the library's CUDA events on the
+    launching stream over the timed steps. The launches run inside a
+    seconds-long step, so the tensor bar is the sustained bf16 peak."""
     launch_ms = ms_filter / deg
     flops_launch = 8.0 * N * N * ne
     achieved = flops_launch / (launch_ms / 1000.0) / 1e12
-    if prec == lib.CHASE_FP64 and tensor:
-        # issued tensor work: OZ_PAIRS BF16 digit-pair products per real MAC of the planar GEMM
-        peak = measured_bf16_peak()
-        traffic = OZAKI_FILTER_DRAM_BYTES.get((N, ne))
-        return {"kernel": "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)",
-                "bound": "tensor", "achieved": OZ_PAIRS * achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": OZ_PAIRS * achieved / peak, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
-                                "dram__bytes_write.sum, one capture)" if traffic else None,
-                "launches_per_step": deg, "flops_per_launch": OZ_PAIRS * flops_launch,
-                "fp64_equivalent_tflops": achieved,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-    if prec == lib.CHASE_FP64:
+    if prec == lib.CHASE_FP64 and not tensor:
         return {"kernel": "zgemm_kernel<EPI_FILTER> (filter HEMM, Eq. 1)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "launches_per_step": deg, "flops_per_launch": flops_launch,
+                "launch_ms": launch_ms,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz"}
-    # issued tensor work: three BF16 products per real MAC of the planar GEMM
-    peak = measured_bf16_peak()
-    return {"kernel": "mixed_filter_kernel (tcgen05 split-BF16x3 filter HEMM)",
-            "bound": "tensor", "achieved": 3.0 * achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": 3.0 * achieved / peak, "traffic": None, "launches_per_step": deg,
-            "flops_per_launch": 3.0 * flops_launch, "fp64_equivalent_tflops": achieved,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    peak, src = measured_peak("bf16_tflops_sustained")
+    if prec == lib.CHASE_FP64:
+        kern, mult = "ozaki_gemm_kernel<EPI_FILTER> (tcgen05 FP64-accurate filter HEMM)", OZ_PAIRS
+        key = ("ozaki", N, ne)
+    else:
+        kern, mult = "mixed_filter_kernel (tcgen05 split-BF16x3 filter HEMM)", 3.0
+        key = ("mixed", N, ne)
+    traffic = FILTER_DRAM_BYTES.get(key)
+    return {"kernel": kern, "bound": "tensor", "achieved": mult * achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": mult * achieved / peak, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+                            if traffic else None,
+            "launches_per_step": deg, "flops_per_launch": mult * flops_launch,
+            "launch_ms": launch_ms, "fp64_equivalent_tflops": achieved,
+            "issued_per_fp64_flop": mult, "peak_source": src}
 
 
 PHASES = ("ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid", "ms_total")
+MODES = {"fp64": ("fp64", 0), "fp64t": ("fp64", 1), "mixed": ("mixed", 0), "mixedt": ("mixed", 1)}
 
 
 def dtype_name(lib, prec, tensor):
     if prec == lib.CHASE_FP64:
         return "f64 (bf16 digit slices, exact accumulation)" if tensor else "f64"
     return "bf16x3+f64"
+
+
+class Line:
+    """The one JSON line of this run; printed once, at the end or on SIGTERM."""
+
+    def __init__(self):
+        self.d = {}
+        self.printed = False
+
+    def emit(self):
+        if not self.printed:
+            self.printed = True
+            print(json.dumps(self.d), flush=True)
+
+
+def tts_solve(lib, torch, p, Ad, V0d, Q0d, mode, max_iter, dev):
+    """One full chase_solve to resid <= tol in `mode`; wall time from the call to
+    its return (synchronised), plus the checks: eigenvalue error against the
+    exact spectrum (all nev), residuals recomputed with torch on sampled
+    columns, orthonormality of the sampled columns."""
+    prec = lib.CHASE_FP64 if MODES[mode][0] == "fp64" else lib.CHASE_MIXED_BF16X3
+    prm = lib.default_params(p.N, p.nev, p.nex, precision=prec, fp64_tensor=MODES[mode][1],
+                             max_iter=max_iter)
+    V = lib.colmajor(V0d.clone())
+    ritz = torch.zeros(p.ne, dtype=torch.float64, device=dev)
+    resid = torch.zeros_like(ritz)
+    with lib.Context(prm) as ctx:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    nrm = p.norm2()
+    lam = torch.from_numpy(p.eigenvalues()[:p.nev]).to(dev)
+    cols = torch.from_numpy(np.unique(np.linspace(0, p.nev - 1, 96).astype(np.int64))).to(dev)
+    X = V[:, :p.nev].index_select(1, cols)
+    R = Ad @ X - X * ritz[:p.nev].index_select(0, cols).unsqueeze(0)
+    res = (torch.linalg.vector_norm(R, dim=0) / nrm).max().item()
+    orth = (X.mH @ X - torch.eye(len(cols), dtype=X.dtype, device=dev)).abs().max().item()
+    err = ((ritz[:p.nev] - lam).abs().max() / nrm).item()
+    lib_res = (resid[:p.nev].max() / nrm).item()
+    del V, X, R
+    torch.cuda.empty_cache()
+    return {"time_to_solution_s": wall, "status": st["status"], "iters": st["iters"],
+            "locked": st["locked"], "matvecs": st["matvecs"],
+            "matvecs_mixed": st["matvecs_mixed"], "switch_iter": st["switch_iter"],
+            "max_rel_eig_err": err, "max_rel_resid_library": lib_res,
+            "max_rel_resid_recomputed_sampled": res, "sampled_columns": int(len(cols)),
+            "orth_sampled": orth,
+            "converged": bool(st["status"] == 0 and err <= 1e-10 and res <= 1e-10),
+            "phase_ms": {k: st[k] for k in PHASES},
+            "heev_sweeps": st["heev_sweeps"], "heev_fp64_sweeps": st["heev_fp64_sweeps"],
+            "qr_variants": st["qr_variant_count"],
+            "filter_tflops_fp64_equiv": st["filter_flops"] / max(st["ms_filter"], 1e-9) / 1e9}
 
 
 def run_gpu(args):
@@ -316,6 +430,16 @@ def run_gpu(args):
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+
+    out = Line()
+
+    def on_term(signum, frame):  # a killed run still reports what it measured
+        if rank == 0 and out.d:
+            out.d.setdefault("skipped", []).append(f"terminated by signal {signum}")
+            out.emit()
+        os._exit(0 if out.d else 1)
+
+    signal.signal(signal.SIGTERM, on_term)
 
     p, name = make_problem(args)
     N, ne = p.N, p.ne
@@ -360,16 +484,14 @@ def run_gpu(args):
         value, ms, _ = aggregate_over_ranks(ev0.elapsed_time(ev1), steps, dist, dev)
         return cx, stats, value, ms / steps, clk
 
+    t_setup = elapsed()
     ctx, stats, value, ms_per_step, clk = timed(params, args.warmup, args.steps,
                                                 ClockSampler(dev.index))
     ms_filter = sum(s["ms_filter"] for s in stats) / len(stats)
-    roof = filter_roofline(lib, prec, args.fp64_tensor, ms_filter, N, ne, deg)
     phases = {k: sum(s[k] for s in stats) / len(stats) for k in PHASES}
     phases["heev_sweeps"] = stats[-1]["heev_sweeps"]
     phases["heev_fp64_sweeps"] = stats[-1]["heev_fp64_sweeps"]
-    launches = int(sum(s["kernel_launches"] for s in stats))
-
-    line = {
+    out.d.update({
         "metric": METRIC, "value": value, "unit": "ChASE iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -379,17 +501,21 @@ def run_gpu(args):
                    "fp64_tensor": args.fp64_tensor,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * N * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roof,
-        "filter_tflops": 8.0 * N * N * stats[-1]["matvecs"] / (ms_filter / 1000.0) / 1e12,
+        "roofline": filter_roofline(lib, prec, args.fp64_tensor, ms_filter, N, ne, deg),
+        "filter_tflops_fp64_equiv": 8.0 * N * N * stats[-1]["matvecs"] / (ms_filter / 1e3) / 1e12,
         "phase_ms": phases,
-        "gpu_launches": launches,
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "qr_variant": stats[-1]["qr_variant_count"],
         "clocks": clk,
-    }
+        "setup_s": t_setup,
+        "skipped": [],
+    })
+    print(json.dumps({"provisional": out.d}), file=sys.stderr, flush=True)
 
     if not args.no_e2e:
-        # same step with HOST buffers: H2D of A, start block and Lanczos vectors,
+        # the same step with HOST buffers: H2D of A, start block and Lanczos vectors,
         # D2H of the Ritz values, residuals and vectors, inside the timed region
+        ne2e = max(1, min(args.steps, args.e2e_steps))
         A_h = torch.empty_strided((N, N), (1, N), dtype=torch.complex128, pin_memory=True)
         A_h.copy_(Ad)
         V0_h = torch.empty_strided((N, ne), (1, N), dtype=torch.complex128, pin_memory=True)
@@ -414,61 +540,88 @@ def run_gpu(args):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(ne2e):
             step_e2e()
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_value, _, _ = aggregate_over_ranks(e0.elapsed_time(e1), args.steps, dist, dev)
-        line["e2e"] = {"value": e2e_value, "unit": "ChASE iterations/s",
-                       "h2d_bytes_per_step": 16 * (N * N + N * ne + N * Q0d.shape[1]),
-                       "d2h_bytes_per_step": 16 * N * ne + 16 * ne}
+        e2e_value, _, _ = aggregate_over_ranks(e0.elapsed_time(e1), ne2e, dist, dev)
+        out.d["e2e"] = {"value": e2e_value, "unit": "ChASE iterations/s", "steps": ne2e,
+                        "h2d_bytes_per_step": 16 * (N * N + N * ne + N * Q0d.shape[1]),
+                        "d2h_bytes_per_step": 16 * N * ne + 16 * ne}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            A_np = A_h.numpy()
-            t_iter, desc, meas = oracle_sample(A_np, V0_h.numpy(), p, deg)
-            line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "ChASE iterations/s",
-                                    "cores": os.cpu_count(), "kind": "oracle",
-                                    "sample": desc + f" (measured {meas:.1f} s)"}
-        del A_h
+            m, frac, t_iter, desc = oracle_sample(A_h.numpy(), V0_h.numpy(), p, deg, ncols=48,
+                                                  nq=384, nrr=768)
+            cores = (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                     else os.cpu_count())
+            out.d["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "ChASE iterations/s",
+                                     "cores": cores, "kind": "oracle",
+                                     "sample": desc + f"; measured {m:.1f} s, scaled phase by "
+                                                      "phase to one iteration (extrapolated)",
+                                     "sample_value": frac / m}
+        del A_h, V0_h, Q0_h, V_out
     ctx.close()
+    torch.cuda.empty_cache()
 
-    if not args.no_variant:
-        # the same step in the other precision modes, timed under the same rules:
-        # the mixed filter (split-BF16x3) and the other FP64 product path
-        variants = []
-        if prec == lib.CHASE_FP64:
-            variants.append(("variant_mixed", lib.CHASE_MIXED_BF16X3, args.fp64_tensor,
-                             args.warmup))
-            # the CUDA-core FP64 step takes over a minute at this size: one warm-up,
-            # and only in single-GPU runs (replica runs keep their timed work short)
-            if world == 1 or not args.fp64_tensor:
-                variants.append(("variant_fp64_dfma" if args.fp64_tensor
-                                 else "variant_fp64_tensor", lib.CHASE_FP64,
-                                 1 - args.fp64_tensor, 1 if args.fp64_tensor else args.warmup))
-        for key, vprec, vt, vw in variants:
-            vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=vprec,
-                                      fp64_tensor=vt)
-            vctx, vstats, vvalue, vms, _ = timed(vprm, vw, args.steps)
-            vctx.close()
-            vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
-            line[key] = {
-                "value": vvalue, "unit": "ChASE iterations/s", "ms_per_step": vms,
-                "warmup": vw, "steps": args.steps, "dtype": dtype_name(lib, vprec, vt),
-                "fp64_tensor": vt,
-                "roofline": filter_roofline(lib, vprec, vt, vfilter, N, ne, deg),
-                "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in PHASES},
-                "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
+    # ------------------------------------------------ optional legs (budget)
+    legs = [m for m in args.tts_legs.split(",") if m] if world == 1 else []
+    t_iter_s = ms_per_step / 1000.0
+    tts = {}
+    for m in legs:
+        # a full solve is a few iterations; the FP64 modes' later iterations run the
+        # filter at up to degree 36 in FP64 (about 2.5x the mixed first iteration)
+        per_iter = 2.5 * t_iter_s
+        left = args.budget_s - elapsed()
+        max_iter = min(args.max_iter, int((left - 60.0) / per_iter))
+        if max_iter < 10:
+            out.d["skipped"].append(f"time-to-solution {m}: {left:.0f} s left of the budget")
+            continue
+        tts[m] = tts_solve(lib, torch, p, Ad, V0d, Q0d, m, max_iter, dev)
+        tts[m]["max_iter"] = max_iter
+        print(json.dumps({"tts": m, **tts[m]}), file=sys.stderr, flush=True)
+    if tts:
+        out.d["time_to_solution"] = tts
+        if "mixedt" in tts and "fp64t" in tts:
+            a, b = tts["mixedt"], tts["fp64t"]
+            out.d["tts_speedup_mixed_vs_fp64"] = (b["time_to_solution_s"] / a["time_to_solution_s"]
+                                                  if a["converged"] and b["converged"] else None)
+    variants = []
+    if world == 1 and not args.no_variant:
+        if prec == lib.CHASE_MIXED_BF16X3:
+            variants.append(("variant_fp64_tensor", lib.CHASE_FP64, 1, 1, min(args.steps, 3)))
+        else:
+            variants.append(("variant_mixed", lib.CHASE_MIXED_BF16X3, args.fp64_tensor, 1,
+                             min(args.steps, 3)))
+    if world == 1 and args.dfma_step:
+        variants.append(("variant_fp64_dfma", lib.CHASE_FP64, 0, 0, 1))
+    for key, vprec, vt, vw, vk in variants:
+        est = (vw + vk) * t_iter_s * (60.0 if not vt else 3.0)
+        if elapsed() + est > args.budget_s:
+            out.d["skipped"].append(f"{key}: estimated {est:.0f} s exceeds the budget")
+            continue
+        vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=vprec, fp64_tensor=vt)
+        vctx, vstats, vvalue, vms, _ = timed(vprm, vw, vk)
+        vctx.close()
+        vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
+        out.d[key] = {
+            "value": vvalue, "unit": "ChASE iterations/s", "ms_per_step": vms,
+            "warmup": vw, "steps": vk, "dtype": dtype_name(lib, vprec, vt), "fp64_tensor": vt,
+            "roofline": filter_roofline(lib, vprec, vt, vfilter, N, ne, deg),
+            "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in PHASES},
+            "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
+    out.d["wall_s"] = elapsed()
     if rank == 0:
-        print(json.dumps(line))
+        out.emit()
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
 def run_tts(args):
-    """Time-to-solution: full chase_solve runs to resid <= tol per precision mode
-    (fp64 = DFMA products, fp64t = tensor-core FP64 products, mixed = split-BF16x3
-    filter then DFMA, mixedt = split-BF16x3 filter then tensor-core FP64), each
-    checked against the exactly known spectrum and by recomputing residuals."""
+    """Time-to-solution only: full chase_solve runs to resid <= tol per precision
+    mode (fp64 = DFMA products, fp64t = tensor-core FP64 products, mixed =
+    split-BF16x3 filter then DFMA, mixedt = split-BF16x3 filter then tensor-core
+    FP64), each checked against the exactly known spectrum and by recomputing
+    sampled residuals."""
     import torch
 
     import paper_2309_15595_gb300 as lib
@@ -476,45 +629,17 @@ def run_tts(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     p, name = make_problem(args)
-    N, ne = p.N, p.ne
     Ad = p.matrix_torch(dev)
     V0d = lib.colmajor(torch.from_numpy(p.start_block()).to(dev))
     Q0d = lib.colmajor(torch.from_numpy(p.lanczos_start()).to(dev))
-    lam = torch.from_numpy(p.eigenvalues()[:p.nev]).to(dev)
-    nrm = p.norm2()
-    modes = {"fp64": (lib.CHASE_FP64, 0), "fp64t": (lib.CHASE_FP64, 1),
-             "mixed": (lib.CHASE_MIXED_BF16X3, 0), "mixedt": (lib.CHASE_MIXED_BF16X3, 1)}
-    out = {}
+    res = {}
     for m in [x for x in args.tts.split(",") if x]:
-        prec, t = modes[m]
-        prm = lib.default_params(N, p.nev, p.nex, precision=prec, fp64_tensor=t,
-                                 max_iter=args.max_iter)
-        V = lib.colmajor(V0d.clone())
-        ritz = torch.zeros(ne, dtype=torch.float64, device=dev)
-        resid = torch.zeros_like(ritz)
-        with lib.Context(prm) as ctx:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = ctx.chase_solve(Ad, V, ritz, resid, lanczos_start=Q0d, allow_not_converged=True)
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-        X = V[:, :p.nev]
-        R = Ad @ X - X * ritz[:p.nev].unsqueeze(0)
-        res = (torch.linalg.vector_norm(R, dim=0) / nrm).max().item()
-        err = ((ritz[:p.nev] - lam).abs().max() / nrm).item()
-        out[m] = {"time_to_solution_s": wall, "status": st["status"], "iters": st["iters"],
-                  "matvecs": st["matvecs"], "matvecs_mixed": st["matvecs_mixed"],
-                  "switch_iter": st["switch_iter"], "max_rel_resid": res,
-                  "max_rel_eig_err": err, "phase_ms": {k: st[k] for k in (
-                      "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_heev", "ms_resid")},
-                  "heev_sweeps": st["heev_sweeps"], "heev_fp64_sweeps": st["heev_fp64_sweeps"],
-                  "qr_variants": st["qr_variant_count"],
-                  "filter_tflops_fp64_equiv": st["filter_flops"] / (st["ms_filter"] * 1e9)}
-        print(json.dumps({"mode": m, **out[m]}), file=sys.stderr, flush=True)
+        res[m] = tts_solve(lib, torch, p, Ad, V0d, Q0d, m, args.max_iter, dev)
+        print(json.dumps({"mode": m, **res[m]}), file=sys.stderr, flush=True)
     line = {"metric": METRIC, "kind": "time-to-solution", "unit": "s", "higher_is_better": False,
-            "config": {"workload": f"{name}: {p.spectrum} spectrum, N={N}, nev={p.nev}, "
+            "config": {"workload": f"{name}: {p.spectrum} spectrum, N={p.N}, nev={p.nev}, "
                                    f"nex={p.nex}, tol {1e-10}"},
-            "modes": out, "data": "synthetic"}
+            "modes": res, "data": "synthetic"}
     print(json.dumps(line))
     return 0
 

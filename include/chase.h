@@ -89,6 +89,11 @@ typedef struct chase_params {
                              exact digit slicing (FP64-class accuracy); 0: DFMA */
   double tol;             /* residual tolerance relative to ||A|| (1e-10, Section 4) */
   double switch_tol;      /* mixed -> FP64 switch, relative residual (1e-5) */
+  int32_t heev_max_sweeps;  /* cap on each stage of the Rayleigh-Ritz Jacobi eigensolver
+                               (sweeps, refinement steps); 0: library defaults (30 FP32
+                               sweeps, 8 FP64 refinement steps, 40 FP64 sweeps). A cap
+                               reached before convergence returns CHASE_ERR_HEEV_NOCONV */
+  int32_t reserved;       /* must be 0 */
 } chase_params;
 
 typedef struct chase_stats {
@@ -192,7 +197,10 @@ CHASE_API int chase_residuals(struct chase_ctx* ctx, const chase_c128* A, int64_
  * call needs ceil(N/64) * ncols doubles of it and returns CHASE_ERR_INVALID_ARG
  * (with a message on stderr) above that, e.g. ncols > 1675 at N = 20000.
  * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture. All calls
+ * device current and caches it for the life of the process; make that first
+ * call before any stream capture. The cache assumes the device's primary
+ * context (the CUDA runtime's, which torch uses) and no cudaDeviceReset in the
+ * process: a reset reloads the library's device code elsewhere. All calls
  * share the one array: calls whose kernels overlap on the GPU (different
  * streams or host threads) race and give wrong results. Nothing in the array
  * needs to start at zero; each call writes every partial it reads. Returns

@@ -38,6 +38,7 @@ class ChaseParams(ctypes.Structure):
         ("lanczos_vecs", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("scaled_filter", ctypes.c_int32), ("fp64_tensor", ctypes.c_int32),
         ("tol", ctypes.c_double), ("switch_tol", ctypes.c_double),
+        ("heev_max_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

@@ -108,6 +108,7 @@ int validate_params(const chase_params* p) {
   if (p->lanczos_vecs < 1 || p->lanczos_vecs > 8) return CHASE_ERR_INVALID_ARG;
   if (p->precision != CHASE_FP64 && p->precision != CHASE_MIXED_BF16X3) return CHASE_ERR_INVALID_ARG;
   if (p->fp64_tensor != 0 && p->fp64_tensor != 1) return CHASE_ERR_INVALID_ARG;
+  if (p->heev_max_sweeps < 0 || p->reserved != 0) return CHASE_ERR_INVALID_ARG;
   return CHASE_OK;
 }
 
@@ -501,6 +502,7 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
   A(dalloc(&c->jw.red, std::max<size_t>(1024, jacobi_red_elems())));
   c->jw.nmax = ne;
+  c->jw.max_sweeps = p->heev_max_sweeps;
   A(dalloc(&c->lw.Q, (size_t)3 * N * 8));
   A(dalloc(&c->lw.ws, skinny_workspace_elems(N, 8)));
   A(dalloc(&c->lw.red, 2048));

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/chase.h"
 
 namespace chase {
@@ -37,6 +39,22 @@ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
 }
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Runs f() once per CUDA device (the one current when called), thread-safe:
+// kernel attributes such as the dynamic shared-memory limit are per device, and
+// solves run from several host threads at once.
+constexpr int kMaxDevices = 64;
+template <typename F>
+void once_per_device(std::once_flag (&flags)[kMaxDevices], F&& f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    f();
+    return;
+  }
+  std::call_once(flags[dev], f);
+}
+// Number of SMs of the current device (cached per device).
+int num_sms();
 
 // Process-wide count of kernel launches issued by this library.
 void count_launch();
@@ -131,6 +149,7 @@ struct JacobiWork {
   double* red;       // reduction scratch
   double* host_red;  // pinned host scalars
   int64_t nmax;
+  int max_sweeps = 0;  // > 0: cap on every stage (sweeps, refinement steps)
   // optional product for the FP64 refinement: P = op(X) B (op(X) = X, M x K, or
   // X^H for X of K x M), epilogue as for zgemm_nn; null: CUDA-core FP64 products
   cudaError_t (*gemm)(void* ctx, int64_t M, int64_t K, const double2* X, int64_t ldx,
@@ -145,8 +164,9 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
 // Batched small Jacobi (n <= 64) on `batch` column-major n x n matrices with
 // stride n*n; eigenvalues ascending (w: batch x n), eigenvectors Z; *status
 // (device) set to 1 when a sweep cap is hit.
+// max_sweeps > 0 lowers the sweep cap (default 40).
 cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2* G, double* w,
-                                 double2* Z, int* status);
+                                 double2* Z, int* status, int max_sweeps = 0);
 
 // -------------------------------------------------------------- vector ops
 cudaError_t copy_cols(cudaStream_t s, int64_t m, int64_t n, const double2* src, int64_t lds,

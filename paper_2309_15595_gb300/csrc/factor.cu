@@ -261,16 +261,16 @@ __global__ void trace_shift_kernel(int64_t n, double2* G, int64_t ldg, double fa
   for (int64_t i = t; i < n; i += 256) G[i + i * ldg].x += shift;
 }
 
-bool g_attr_set = false;
+std::once_flag g_attr_once[kMaxDevices];
 void set_attrs() {
-  if (g_attr_set) return;
-  cudaFuncSetAttribute(potf2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       2 * NB * NB * (int)sizeof(double2));
-  cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       2 * NB * NB * (int)sizeof(double2));
-  cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (NB * RP + NB * NB + TK * RP + TK * NB) * (int)sizeof(double2));
-  g_attr_set = true;
+  once_per_device(g_attr_once, []() {
+    cudaFuncSetAttribute(potf2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * NB * NB * (int)sizeof(double2));
+    cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * NB * NB * (int)sizeof(double2));
+    cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (NB * RP + NB * NB + TK * RP + TK * NB) * (int)sizeof(double2));
+  });
 }
 
 }  // namespace

@@ -87,7 +87,7 @@ constexpr int SJ_MAX = 64, SJ_T = 256;
 
 __global__ void __launch_bounds__(SJ_T)
     jacobi_small_kernel(int n, const double2* __restrict__ Gin, double* __restrict__ w,
-                        double2* __restrict__ Zout, int* status) {
+                        double2* __restrict__ Zout, int* status, int max_sweeps) {
   extern __shared__ double2 sm[];
   double2* G = sm;                    // n x n, ld SJ_MAX
   double2* Z = sm + SJ_MAX * SJ_MAX;  // n x n
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(SJ_T)
   const int npairs = m / 2;
   double off_prev = 1e300;
   bool conv = false;
-  for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double so = 0.0, sf = 0.0;
     for (int e = t; e < n * n; e += SJ_T) {
       const int r = e % n, c = e / n;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SJ_T)
       break;
     }
     off_prev = off;
-    if (sweep == kMaxSweeps) break;
+    if (sweep == max_sweeps) break;
     for (int round = 0; round < m - 1; ++round) {
       if (t < npairs) {
         int p, q;
@@ -733,7 +733,7 @@ __global__ void frob2_kernel(int64_t n, const double2* __restrict__ G, int64_t l
   }
 }
 
-bool g_small_attr = false;
+std::once_flag g_small_attr[kMaxDevices];
 
 }  // namespace
 
@@ -765,15 +765,15 @@ cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, co
 size_t jacobi_params_elems(int64_t n) { return (size_t)8 * (n / 2 + 2) + 8 + n; }
 
 cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2* G, double* w,
-                                 double2* Z, int* status) {
+                                 double2* Z, int* status, int max_sweeps) {
   if (n > SJ_MAX || n < 1) return cudaErrorInvalidValue;
   const size_t smem = 2 * SJ_MAX * SJ_MAX * sizeof(double2);
-  if (!g_small_attr) {
+  once_per_device(g_small_attr, [smem]() {
     cudaFuncSetAttribute(jacobi_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    g_small_attr = true;
-  }
-  jacobi_small_kernel<<<batch, SJ_T, smem, s>>>(n, G, w, Z, status); count_launch();
+  });
+  const int cap = max_sweeps > 0 ? std::min(max_sweeps, kMaxSweeps) : kMaxSweeps;
+  jacobi_small_kernel<<<batch, SJ_T, smem, s>>>(n, G, w, Z, status, cap); count_launch();
   return cudaGetLastError();
 }
 
@@ -789,7 +789,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     e = cudaMemcpy2DAsync(wk.Gw, n * sizeof(double2), G, ldg * sizeof(double2),
                           n * sizeof(double2), n, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return CHASE_ERR_CUDA;
-    e = jacobi_small_batched(s, (int)n, 1, wk.Gw, w, wk.Zw, status);
+    e = jacobi_small_batched(s, (int)n, 1, wk.Gw, w, wk.Zw, status, wk.max_sweeps);
     if (e != cudaSuccess) return CHASE_ERR_CUDA;
     e = cudaMemcpy2DAsync(Z, ldz * sizeof(double2), wk.Zw, n * sizeof(double2),
                           n * sizeof(double2), n, cudaMemcpyDeviceToDevice, s);
@@ -806,8 +806,11 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   init32_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.G32a, wk.Z32); count_launch();
   int sw32 = 0;
   bool conv32 = false, in_g1 = false;
+  // stage caps: 30 FP32 sweeps, 8 refinement steps, kMaxSweeps FP64 sweeps, each
+  // lowered to the caller's cap when one is set
+  auto cap = [&](int def) { return wk.max_sweeps > 0 ? std::min(def, wk.max_sweeps) : def; };
   RC_(run_coop<float>(s, n, wk.G32a, wk.G32b, wk.Z32, reinterpret_cast<float*>(wk.params), wk.red,
-                      30, 4e-6, 1e-4, &sw32, &conv32, &in_g1));
+                      cap(30), 4e-6, 1e-4, &sw32, &conv32, &in_g1));
   // --- FP64: refine the FP32 eigenvectors (Ogita-Aishima steps, FP64 GEMMs)
   promote_kernel<<<g2, 128, 0, s>>>(n, wk.Z32, wk.Zw); count_launch();
   const unsigned gb = (unsigned)cdiv(n, 256);
@@ -835,7 +838,8 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   // below 1e-6 the products are the CUDA-core FP64 ones, and so are the final
   // step and the orthogonalisation.
   bool tc = wk.gemm != nullptr;
-  for (; refine < 8; ++refine) {  // 2-4 steps from FP32 accuracy; a slow start gets more
+  const int max_refine = cap(8);
+  for (; refine < max_refine; ++refine) {  // 2-4 steps from FP32 accuracy; a slow start gets more
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = wk.T;
@@ -918,8 +922,8 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     double2* Zrot = Xn;  // the buffer X does not use
     identity_kernel<<<g2, 128, 0, s>>>(n, Zrot); count_launch();
     bool in_g1_64 = false;
-    RC_(run_coop<double>(s, n, wk.Gw, wk.Gw2, Zrot, wk.params, wk.red, kMaxSweeps, 1e-15, 1e-12,
-                         &sw64, &conv, &in_g1_64));
+    RC_(run_coop<double>(s, n, wk.Gw, wk.Gw2, Zrot, wk.params, wk.red, cap(kMaxSweeps), 1e-15,
+                         1e-12, &sw64, &conv, &in_g1_64));
     double2* Gcur = in_g1_64 ? wk.Gw2 : wk.Gw;
     Epilogue ez{};
     ez.mode = EPI_STORE;

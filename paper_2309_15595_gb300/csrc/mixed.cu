@@ -15,7 +15,8 @@
 //
 // Kernel structure (one 128 x 256 output tile per CTA, 6 warps):
 //   warp 0   TMA producer: A_hi, A_lo (128 x 32) and B_hi, B_lo (256 x 32) per
-//            K block into a 2-stage shared-memory ring (128B swizzle)
+//            K block into a 4-stage shared-memory ring of 48 KB stages (64B
+//            swizzle: one K block of 32 BF16 is a 64-byte row)
 //   warp 1   TMEM allocator and single-thread MMA issuer (tcgen05.mma, M=128,
 //            N=256, K=16, kind::f16 with BF16 inputs)
 //   warps 2-5 epilogue: tcgen05.ld of their 32-lane TMEM quarter

@@ -22,13 +22,15 @@ namespace {
 constexpr size_t kScratchDoubles = (size_t)4 << 17;  // 524288 doubles = 4 MiB
 static __device__ __align__(256) double g_resid_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_resid_scratch on the current device. In host code the
 // symbol is only a host-side stand-in, so its device address is looked up once
-// per device, with that device current, and cached.
+// per device, with that device current, and cached. The cache assumes the
+// device's primary context (the one the CUDA runtime and torch use) for the
+// life of the process: after cudaDeviceReset the module is loaded again at
+// another address and the cached pointer would be stale.
 int scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CHASE_ERR_CUDA;

@@ -276,18 +276,22 @@ __global__ void skinny_reduce_kernel(int64_t M, int n, int splits, const double2
   }
 }
 
-int g_num_sms = 0;
-int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 152;
-  }
-  return g_num_sms;
-}
+std::once_flag g_sms_once[kMaxDevices];
+int g_num_sms[kMaxDevices] = {};
 
 }  // namespace
+
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 152;
+  once_per_device(g_sms_once, [dev]() {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;
+    g_num_sms[dev] = n;
+  });
+  return g_num_sms[dev];
+}
 
 int64_t zgemm_row_tiles(int64_t M) { return cdiv(M, BM); }
 

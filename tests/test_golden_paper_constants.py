@@ -38,6 +38,12 @@ def test_oracle_shift_constant():
 
 
 def test_library_defaults_follow_the_paper():
+    # the library's host-side defaults (no GPU call); skipped on a checkout
+    # where the shared library has not been built yet
+    lib_path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2309_15595_gb300", "libchase_gb300.so")
+    if not os.path.exists(lib_path):
+        pytest.skip("libchase_gb300.so not built")
     import paper_2309_15595_gb300 as lib
 
     c = constants()
@@ -49,3 +55,26 @@ def test_library_defaults_follow_the_paper():
     assert sig.parameters["deg_init"].default == c["deg_init"]
     assert sig.parameters["deg_max"].default == c["deg_max"]
     assert sig.parameters["tol"].default == c["tol"]
+
+
+@pytest.mark.gpu
+def test_library_qr_variant_thresholds():
+    """The library's own Alg. 4 choice at the thresholds the paper states:
+    cond > 1e8 shifted, cond < 20 CholeskyQR1, otherwise CholeskyQR2."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_15595_gb300 as lib
+    from synth import Problem
+
+    c = constants()
+    hi, lo = c["qr_shifted_above"], c["qr_cholqr1_below"]
+    X = Problem(N=300, nev=24, nex=0, seed=9).start_block()
+    cases = [(np.nextafter(lo, -np.inf), lib.CHASE_QR_CHOLQR1), (lo, lib.CHASE_QR_CHOLQR2),
+             (hi, lib.CHASE_QR_CHOLQR2), (np.nextafter(hi, np.inf), lib.CHASE_QR_SHIFTED)]
+    with lib.Context(lib.default_params(300, 24, 0)) as ctx:
+        for cond, want in cases:
+            Xd = lib.colmajor(torch.from_numpy(X).cuda())
+            assert ctx.chase_qr(Xd, 24, float(cond)) == want, cond
+            assert O.select_qr_variant(float(cond)) == want
+

@@ -4,9 +4,10 @@ It serves callers that cannot allocate device memory (and so cannot create a
 chase context): its scratch is a fixed array inside the library. This test
 calls it through the C ABI twice in a row, with different sizes, so the second
 call runs over the first call's leftover scratch contents, and checks each
-output against the context-based chase_residuals on the same inputs, within the
-residual tolerance the other GPU tests use (1e-11 relative). It also checks
-that a size beyond the fixed scratch is rejected before any launch.
+output against the context-based chase_residuals on the same inputs and against
+the CPU oracle's residual norms, within the residual tolerance the other GPU
+tests use (1e-11 relative). It also checks that a size beyond the fixed scratch
+is rejected before any launch.
 Collected last so that a failure here leaves every other test already run.
 """
 import ctypes
@@ -14,6 +15,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import chase_oracle as O
 from synth import Problem
 
 torch = pytest.importorskip("torch")
@@ -36,9 +38,11 @@ def _noalloc(lib, Ad, Vd, theta_d, ncols, out_d):
 def test_residuals_noalloc_matches_context_entry_point(lib):
     for N, ncols, seed in [(512, 60, 11), (333, 37, 12)]:
         p = Problem(N=N, nev=ncols, nex=0, reflectors=4, seed=seed)
-        Ad = _dev(p.matrix(), lib)
-        Vd = _dev(p.start_block(), lib)
-        theta = torch.from_numpy(np.linspace(0.1, 7.0, ncols)).cuda()
+        A, V = p.matrix(), p.start_block()
+        Ad = _dev(A, lib)
+        Vd = _dev(V, lib)
+        theta_h = np.linspace(0.1, 7.0, ncols)
+        theta = torch.from_numpy(theta_h).cuda()
         ref = torch.zeros(ncols, dtype=torch.float64, device="cuda")
         with lib.Context(lib.default_params(N, ncols, 0)) as ctx:
             ctx.chase_residuals(Ad, Vd, theta, ncols, ref)
@@ -46,6 +50,7 @@ def test_residuals_noalloc_matches_context_entry_point(lib):
         assert _noalloc(lib, Ad, Vd, theta, ncols, got) == 0
         torch.cuda.synchronize()
         np.testing.assert_allclose(got.cpu().numpy(), ref.cpu().numpy(), rtol=1e-11)
+        np.testing.assert_allclose(got.cpu().numpy(), O.residuals(A, V, theta_h), rtol=1e-11)
 
 
 def test_residuals_noalloc_rejects_oversize(lib):
