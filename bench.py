@@ -409,6 +409,8 @@ def tts_solve(lib, torch, p, Ad, V0d, Q0d, mode, max_iter, dev):
             "converged": bool(st["status"] == 0 and err <= 1e-10 and res <= 1e-10),
             "phase_ms": {k: st[k] for k in PHASES},
             "heev_sweeps": st["heev_sweeps"], "heev_fp64_sweeps": st["heev_fp64_sweeps"],
+            "heev_cluster_solves": st["heev_cluster_solves"],
+            "heev_cluster_max": st["heev_cluster_max"],
             "qr_variants": st["qr_variant_count"],
             "filter_tflops_fp64_equiv": st["filter_flops"] / max(st["ms_filter"], 1e-9) / 1e9}
 
@@ -491,6 +493,8 @@ def run_gpu(args):
     phases = {k: sum(s[k] for s in stats) / len(stats) for k in PHASES}
     phases["heev_sweeps"] = stats[-1]["heev_sweeps"]
     phases["heev_fp64_sweeps"] = stats[-1]["heev_fp64_sweeps"]
+    phases["heev_cluster_solves"] = stats[-1]["heev_cluster_solves"]
+    phases["heev_cluster_max"] = stats[-1]["heev_cluster_max"]
     out.d.update({
         "metric": METRIC, "value": value, "unit": "ChASE iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

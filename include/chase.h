@@ -45,7 +45,8 @@ typedef enum chase_status {
   CHASE_ERR_INVALID_ARG = 1,   /* bad size, pointer, degree or parameter */
   CHASE_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
   CHASE_ERR_OOM = 3,           /* workspace allocation failed in chase_create */
-  CHASE_ERR_QR_BREAKDOWN = 4,  /* every CholeskyQR variant and the fallback failed */
+  CHASE_ERR_QR_BREAKDOWN = 4,  /* the QR met non-finite values (the Householder
+                                  fallback of Alg. 4 does not break down otherwise) */
   CHASE_ERR_HEEV_NOCONV = 5,   /* Jacobi sweep cap reached before convergence */
   CHASE_ERR_NOT_CONVERGED = 6  /* max_iter reached; outputs hold the best pairs */
 } chase_status;
@@ -64,8 +65,9 @@ enum {
   CHASE_QR_CHOLQR1 = 1,
   CHASE_QR_CHOLQR2 = 2,
   CHASE_QR_SHIFTED = 3,   /* shifted CholeskyQR pass + CholeskyQR2 */
-  CHASE_QR_FALLBACK = 4   /* POTRF failed inside the shifted branch: repeated
-                             shifted passes, then CholeskyQR2 */
+  CHASE_QR_HOUSEHOLDER = 4, /* a POTRF of the shifted branch failed: Householder QR
+                               of the input block (Alg. 4 fallback) */
+  CHASE_QR_FALLBACK = CHASE_QR_HOUSEHOLDER  /* former name of the same code */
 };
 
 typedef struct chase_c128 { double re, im; } chase_c128;
@@ -111,6 +113,9 @@ typedef struct chase_stats {
                              refinement steps and FP64 Jacobi sweeps */
   int32_t heev_fp64_sweeps;  /* Jacobi heev: FP64 sweeps run for pairs the refinement could not separate */
   double ms_heev;         /* part of ms_rr spent in the Jacobi eigensolver */
+  int32_t heev_cluster_solves;  /* Rayleigh-Ritz eigensolves whose near-degenerate pairs were
+                                   finished cluster by cluster (no full FP64 sweep) */
+  int32_t heev_cluster_max;     /* largest such cluster over the solve */
 } chase_stats;
 
 /* Fills *p with the defaults above for the given sizes. Host only. */
@@ -165,8 +170,14 @@ CHASE_API int chase_filter(struct chase_ctx* ctx, const chase_c128* A, int64_t l
 /* 1D-CAQR of Alg. 4 on V[:, 0:ncols] (ncols <= nev+nex), in place: V becomes
  * Q with V_in = Q R, R upper triangular with positive real diagonal. The
  * variant follows cond_est (> 1e8 shifted, < 20 CholeskyQR1, else
- * CholeskyQR2); *variant_used (host, may be NULL) receives a CHASE_QR_* code.
- * Synchronises (POTRF info is a host decision). */
+ * CholeskyQR2); a CholeskyQR1/2 whose POTRF fails re-runs the shifted branch,
+ * and a shifted branch whose POTRF fails (or that of the CholeskyQR2 after it)
+ * reverts to Householder QR of the input block (Alg. 4). *variant_used (host,
+ * may be NULL) receives a CHASE_QR_* code. Synchronises (POTRF info is a host
+ * decision). Unlike Alg. 2, which runs the QR on all nev + nex columns and then
+ * restores the locked ones from C2, this call factors exactly the columns it is
+ * given: chase_solve does the restore itself, and a caller that wants it passes
+ * the full block and copies its locked columns back. */
 CHASE_API int chase_qr(struct chase_ctx* ctx, chase_c128* V, int64_t ldv, int64_t ncols,
              double cond_est, int32_t* variant_used);
 

@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     CHASE_QR_CHOLQR1,
     CHASE_QR_CHOLQR2,
     CHASE_QR_FALLBACK,
+    CHASE_QR_HOUSEHOLDER,
     CHASE_QR_SHIFTED,
     ChaseParams,
     ChaseStats,

@@ -26,7 +26,8 @@ CHASE_MIXED_BF16X3 = 1
 CHASE_QR_CHOLQR1 = 1
 CHASE_QR_CHOLQR2 = 2
 CHASE_QR_SHIFTED = 3
-CHASE_QR_FALLBACK = 4
+CHASE_QR_HOUSEHOLDER = 4
+CHASE_QR_FALLBACK = CHASE_QR_HOUSEHOLDER  # former name
 
 
 class ChaseParams(ctypes.Structure):
@@ -57,6 +58,7 @@ class ChaseStats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("heev_sweeps", ctypes.c_int32), ("heev_fp64_sweeps", ctypes.c_int32),
         ("ms_heev", ctypes.c_double),
+        ("heev_cluster_solves", ctypes.c_int32), ("heev_cluster_max", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -79,12 +79,14 @@ void free_ctx(chase_ctx* c) {
   void* bufs[] = {c->V2, c->W, c->G, c->Yeig, c->gram_ws, c->dinv, c->info, c->resid_partial,
                   c->dscal, c->perm_d, c->jw.Gw, c->jw.Gw2, c->jw.Zw, c->jw.Zw2, c->jw.T,
                   c->jw.G32a, c->jw.G32b, c->jw.Z32, c->jw.params, c->jw.red,
+                  c->jw.pairs, c->jw.npairs, c->jw.cl_idx, c->jw.cl_off,
                   c->lw.Q, c->lw.ws, c->lw.red, c->lw.ab, c->lw.T, c->lw.theta, c->lw.Z,
                   c->lw.out4, c->lw.status};
   for (void* b : bufs)
     if (b) cudaFree(b);
   mixed_free(c->mw);
   ozaki_free(c->ow);
+  householder_free(c->hw);
   if (c->oz_partial) cudaFree(c->oz_partial);
   if (c->gw) cudaFree(c->gw);
   if (c->gd) cudaFree(c->gd);
@@ -217,65 +219,117 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 // ---------------------------------------------------------------------- QR
 // One CholeskyQR pass (Alg. 3 body): G = X^H X (+ s I), G = U^H U, X = X U^-1.
 // Returns the POTRF info through *info_h (0 = success; X untouched otherwise).
-// With the tensor-core FP64 products, the Gram matrix of every pass but the
-// last is a digit-sliced product (error about sqrt(N) 2^-47 of the column
-// maxima; the next pass removes what it leaves). The last pass of a variant
-// fixes the orthogonality, which is about kappa(X)^2 times the Gram error, so
-// it keeps the FP64 CUDA-core Gram. X U^-1 is always the FP64 triangular
-// solve: a fixed-point product with U^-1 (whose columns mix entries of very
-// different magnitude for a filtered block) would lose the small entries.
+//
+// With the tensor-core FP64 products (fp64_tensor):
+//  * Gram matrix. A digit-sliced X^H X has an error of about sqrt(N) 2^-47 of
+//    the column maxima (FP64: sqrt(N) 2^-53); the orthogonality a pass delivers
+//    is about kappa(X)^2 times the Gram error. A pass that is not the last of
+//    its variant (its error is removed by the next pass) and the last pass of
+//    CholeskyQR2 / shifted CholeskyQR2 (whose input is already orthonormal to
+//    about the previous pass's kappa^2 u) use the tensor cores; CholeskyQR1's
+//    single pass (kappa up to 20) keeps the FP64 CUDA-core Gram. A last pass
+//    whose U turns out not to be near the identity (max |U - I| > 1e-3, so the
+//    input was not near-orthonormal) recomputes its Gram in FP64 before using it.
+//  * X U^-1. When max |U - I| <= 1e-3, X U^-1 = X + X D with D = U^-1 - I
+//    (|D| ~ 1e-3 or less): the digit-sliced product X D then carries an error of
+//    about sqrt(n) 2^-46 |X| |D|, below 1e-15 of |X|, so it runs on the tensor
+//    cores (U^-1 by a recursive blocked inversion with FP64 GEMMs). Otherwise
+//    X U^-1 is the FP64 triangular solve: a digit-sliced product with a general
+//    U^-1, whose columns mix entries of very different size for a filtered
+//    block, would keep the small entries only to 2^-48 of their column's
+//    largest and lose the span of the small columns.
+constexpr double kNearIdentity = 1e-3;
+
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
-                bool last, int* info_h) {
-  const bool tc = c->p.fp64_tensor && !last;
-  if (tc) {
-    Epilogue ep{};
-    ep.mode = EPI_STORE;
-    ep.Y = c->G;
-    ep.ldy = c->ne;
-    CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow));
-    CK(hermitian_part(c->stream, n, c->G, c->ne));
-  } else {
-    CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
-             c->gram_ws_elems));
+                bool tc_gram, bool last, int* info_h) {
+  const bool tensor = c->p.fp64_tensor != 0;
+  bool tc = tensor && tc_gram;
+  double* dev_h = c->host + 2 * c->ne + 10;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (tc) {
+      Epilogue ep{};
+      ep.mode = EPI_STORE;
+      ep.Y = c->G;
+      ep.ldy = c->ne;
+      CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow));
+      CK(hermitian_part(c->stream, n, c->G, c->ne));
+    } else {
+      CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
+               c->gram_ws_elems));
+    }
+    if (shift_factor > 0.0) CK(add_trace_shift(c->stream, n, c->G, c->ne, shift_factor, c->dscal));
+    CK(potrf_upper(c->stream, n, c->G, c->ne, c->dinv, c->info));
+    if (tensor) CK(max_dev_identity(c->stream, n, c->G, c->ne, c->dscal + 1));
+    CK(cudaMemcpyAsync(info_h, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (tensor)
+      CK(cudaMemcpyAsync(dev_h, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (tc) RC(ozaki_check(c->stream, c->ow));
+    if (*info_h != 0) return CHASE_OK;
+    // a last pass whose input was not near-orthonormal: FP64 Gram after all
+    if (tc && last && !(*dev_h <= kNearIdentity)) {
+      tc = false;
+      continue;
+    }
+    break;
   }
-  if (shift_factor > 0.0) CK(add_trace_shift(c->stream, n, c->G, c->ne, shift_factor, c->dscal));
-  CK(potrf_upper(c->stream, n, c->G, c->ne, c->dinv, c->info));
+  if (tensor && *dev_h <= kNearIdentity) {
+    // X <- X + X (U^-1 - I) on the tensor cores; U^-1 (recursive blocked
+    // inverse, FP64 GEMMs) into Yeig, which is free during the QR
+    CK(triangular_inverse(c->stream, n, c->G, c->ne, c->dinv, c->Yeig, c->ne, c->jw.T));
+    CK(set_identity(c->stream, n, c->Yeig, c->ne, true));
+    Epilogue ep{};
+    ep.mode = EPI_FILTER;  // X = (X D) + X, in place: the product reads X's digit planes
+    ep.alpha = 1.0;
+    ep.beta = 1.0;
+    ep.gamma = 0.0;
+    ep.X = X;
+    ep.ldx = ldx;
+    ep.Y = X;
+    ep.ldy = ldx;
+    CK(ozaki_gemm_general(c->stream, c->N, n, X, ldx, false, n, c->Yeig, c->ne, ep, c->ow));
+    return ozaki_check(c->stream, c->ow);
+  }
   CK(trsm_right_upper(c->stream, c->N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
-  CK(cudaMemcpyAsync(info_h, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (tc) RC(ozaki_check(c->stream, c->ow));
   return CHASE_OK;
 }
 
 int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32_t* variant) {
   int* info_h = reinterpret_cast<int*>(c->host + 2 * c->ne + 8);
+  // the input block is kept in W (free while the QR runs) for the Householder
+  // fallback, which factors the block the caller passed in
+  CK(copy_cols(c->stream, c->N, n, X, ldx, c->W, c->N));
   int v = cond > 1e8 ? CHASE_QR_SHIFTED : (cond < 20 ? CHASE_QR_CHOLQR1 : CHASE_QR_CHOLQR2);
   if (v != CHASE_QR_SHIFTED) {
     const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
     bool ok = true;
     for (int k = 0; k < passes && ok; ++k) {
-      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, info_h));
+      // CholeskyQR1's single pass keeps the FP64 Gram (see cholqr_pass)
+      RC(cholqr_pass(c, X, ldx, n, 0.0, passes == 2, k == passes - 1, info_h));
       ok = (*info_h == 0);
     }
     if (ok) {
       if (variant) *variant = v;
       return CHASE_OK;
     }
-    v = CHASE_QR_SHIFTED;  // reading: a failed CholeskyQR1/2 re-runs the shifted branch
+    // reading: Alg. 4 names no fallback for CholeskyQR1/2; a failed POTRF there
+    // (the estimate was too low) re-runs the shifted branch on the input block
+    CK(copy_cols(c->stream, c->N, n, c->W, c->N, X, ldx));
   }
-  // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2
+  // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2, then CholeskyQR2
   const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    RC(cholqr_pass(c, X, ldx, n, factor, false, info_h));
-    if (*info_h != 0) return CHASE_ERR_QR_BREAKDOWN;
-    RC(cholqr_pass(c, X, ldx, n, 0.0, false, info_h));
-    if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, info_h));
-    if (*info_h == 0) {
-      if (variant) *variant = attempt == 0 ? CHASE_QR_SHIFTED : CHASE_QR_FALLBACK;
-      return CHASE_OK;
-    }
+  RC(cholqr_pass(c, X, ldx, n, factor, true, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, true, info_h));
+  if (*info_h == 0) {
+    if (variant) *variant = CHASE_QR_SHIFTED;
+    return CHASE_OK;
   }
-  return CHASE_ERR_QR_BREAKDOWN;
+  // Alg. 4: a POTRF of the shifted branch failed -> Householder QR of the input
+  // (reading: also when the failure is in the CholeskyQR2 after the shift)
+  RC(householder_qr(c->stream, c->N, n, c->W, c->N, X, ldx, c->hw, c->gram_ws, c->gram_ws_elems));
+  if (variant) *variant = CHASE_QR_HOUSEHOLDER;
+  return CHASE_OK;
 }
 
 // ----------------------------------------------------------- Rayleigh-Ritz
@@ -311,9 +365,9 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
       cudaEventCreate(&h1);
       cudaEventRecord(h0, c->stream);
     }
-    int sweeps64 = 0;
-    const int rc =
-        jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps, &sweeps64);
+    int sweeps64 = 0, cl[3] = {0, 0, 0};
+    const int rc = jacobi_heev(c->stream, n, c->G, c->ne, ritz, c->Yeig, c->ne, c->jw, &sweeps,
+                               &sweeps64, cl);
     if (st) {
       cudaEventRecord(h1, c->stream);
       cudaEventSynchronize(h1);
@@ -322,6 +376,8 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
       st->ms_heev += ms;
       st->heev_sweeps += sweeps;
       st->heev_fp64_sweeps += sweeps64;
+      st->heev_cluster_solves += cl[0];
+      st->heev_cluster_max = std::max(st->heev_cluster_max, cl[1]);
       cudaEventDestroy(h0);
       cudaEventDestroy(h1);
     }
@@ -501,6 +557,10 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->jw.Z32, (size_t)ne * ne));
   A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
   A(dalloc(&c->jw.red, std::max<size_t>(1024, jacobi_red_elems())));
+  A(dalloc(&c->jw.pairs, (size_t)2 * kMaxClusterPairs));
+  A(dalloc(&c->jw.npairs, 1));
+  A(dalloc(&c->jw.cl_idx, (size_t)ne));
+  A(dalloc(&c->jw.cl_off, (size_t)ne + 1));
   c->jw.nmax = ne;
   c->jw.max_sweeps = p->heev_max_sweeps;
   A(dalloc(&c->lw.Q, (size_t)3 * N * 8));
@@ -512,6 +572,7 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->lw.Z, (size_t)8 * 64 * 64));
   A(dalloc(&c->lw.out4, 4));
   A(dalloc(&c->lw.status, 4));
+  if (ok) A(householder_alloc(c->hw, N, ne));
   if (ok && p->precision == CHASE_MIXED_BF16X3) A(mixed_alloc(c->mw, N, ne));
   if (ok && p->fp64_tensor) {
     A(ozaki_alloc(c->ow, N, ne));

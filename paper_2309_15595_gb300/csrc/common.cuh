@@ -108,6 +108,15 @@ cudaError_t potrf_upper(cudaStream_t s, int64_t n, double2* G, int64_t ldg, doub
 cudaError_t trsm_right_upper(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx,
                              const double2* U, int64_t ldu, const double2* dinv,
                              const int* info);
+// Y = U^{-1} (n x n, ld ldy, upper triangular) from potrf_upper's U and dinv;
+// T: scratch of at least n^2 / 4 + n entries.
+cudaError_t triangular_inverse(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
+                               const double2* dinv, double2* Y, int64_t ldy, double2* T);
+// *out (device) = max over the upper triangle of |U_ij - delta_ij|.
+cudaError_t max_dev_identity(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
+                             double* out);
+// M = I, or M -= I with subtract (n x n, ld ldm).
+cudaError_t set_identity(cudaStream_t s, int64_t n, double2* M, int64_t ldm, bool subtract);
 // G_ii += shift * trace(G) (device scalars only); used for the shifted pass.
 cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double factor,
                             double* scratch);
@@ -150,6 +159,10 @@ struct JacobiWork {
   double* host_red;  // pinned host scalars
   int64_t nmax;
   int max_sweeps = 0;  // > 0: cap on every stage (sweeps, refinement steps)
+  int* pairs = nullptr;   // index pairs the refinement could not separate (2 ints each)
+  int* npairs = nullptr;  // their count (device)
+  int* cl_idx = nullptr;  // clustered column indices, grouped by cluster (n ints)
+  int* cl_off = nullptr;  // cluster offsets into cl_idx (n + 1 ints)
   // optional product for the FP64 refinement: P = op(X) B (op(X) = X, M x K, or
   // X^H for X of K x M), epilogue as for zgemm_nn; null: CUDA-core FP64 products
   cudaError_t (*gemm)(void* ctx, int64_t M, int64_t K, const double2* X, int64_t ldx,
@@ -158,9 +171,14 @@ struct JacobiWork {
   void* gemm_ctx = nullptr;
 };
 size_t jacobi_params_elems(int64_t n);
+constexpr int kMaxClusterPairs = 1 << 16;  // capacity of JacobiWork::pairs
 size_t jacobi_red_elems();  // doubles of JacobiWork::red
+// cluster_out (3 ints, may be null): [0] 1 if the pairs the FP64 refinement
+// could not separate were finished cluster by cluster, [1] the largest cluster,
+// [2] the number of clusters (or of recorded pairs when the full FP64 sweeps ran).
 int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
-                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out = nullptr);
+                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out = nullptr,
+                int* cluster_out = nullptr);
 // Batched small Jacobi (n <= 64) on `batch` column-major n x n matrices with
 // stride n*n; eigenvalues ascending (w: batch x n), eigenvectors Z; *status
 // (device) set to 1 when a sweep cap is hit.

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "householder.cuh"
 #include "mixed.cuh"
 #include "ozaki.cuh"
 #include "../../include/chase.h"
@@ -29,6 +30,7 @@ struct chase_ctx {
   chase::LanczosWork lw{};
   chase::MixedWork mw{};
   chase::OzakiWork ow{};
+  chase::HouseholderWork hw{};  // Householder QR fallback of Alg. 4
   double* oz_partial = nullptr;  // residual partials of the tensor-core path (32-row tiles)
   bool oz_a_valid = false;       // digits of the current solve's A are prepared
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -261,6 +261,81 @@ __global__ void trace_shift_kernel(int64_t n, double2* G, int64_t ldg, double fa
   for (int64_t i = t; i < n; i += 256) G[i + i * ldg].x += shift;
 }
 
+// max over the upper triangle of |U_ij - delta_ij| (one CTA, fixed order)
+__global__ void __launch_bounds__(1024)
+    dev_identity_kernel(int64_t n, const double2* __restrict__ U, int64_t ldu,
+                        double* __restrict__ out) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  for (int64_t e = threadIdx.x; e < n * n; e += 1024) {
+    const int64_t i = e % n, j = e / n;
+    if (i > j) continue;
+    double2 u = U[i + j * ldu];
+    if (i == j) u.x -= 1.0;
+    m = fmax(m, sqrt(u.x * u.x + u.y * u.y));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 512; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// M = I (set) or M -= I (subtract), n x n, ld ldm
+__global__ void identity_kernel(int64_t n, double2* __restrict__ M, int64_t ldm, bool subtract) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n) return;
+  if (subtract) {
+    if (i == j) M[i + j * ldm].x -= 1.0;
+  } else {
+    M[i + j * ldm] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// kb x kb diagonal-block inverse (ld NB) into the diagonal block of Y (ld ldy)
+__global__ void copy_dinv_kernel(int kb, const double2* __restrict__ W, double2* __restrict__ Y,
+                                 int64_t ldy) {
+  const int r = threadIdx.x, c = blockIdx.x;
+  if (r < kb && c < kb) Y[r + (int64_t)c * ldy] = r <= c ? W[r + c * NB] : make_double2(0.0, 0.0);
+}
+
+// Y = U^{-1} for the leading n x n block of U (upper triangular, diagonal-block
+// inverses in dinv, block b at dinv + b NB^2), recursively:
+// inv([[U11, U12], [0, U22]]) = [[Y11, -Y11 U12 Y22], [0, Y22]], split at a
+// multiple of NB so the leaves are the stored diagonal-block inverses.
+cudaError_t trinv_rec(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
+                      const double2* dinv, double2* Y, int64_t ldy, double2* T) {
+  if (n <= NB) {
+    copy_dinv_kernel<<<(unsigned)n, NB, 0, s>>>((int)n, dinv, Y, ldy); count_launch();
+    return cudaGetLastError();
+  }
+  const int64_t n1 = cdiv(cdiv(n, 2), NB) * NB, n2 = n - n1;
+  cudaError_t e = trinv_rec(s, n1, U, ldu, dinv, Y, ldy, T);
+  if (e != cudaSuccess) return e;
+  e = trinv_rec(s, n2, U + n1 + n1 * ldu, ldu, dinv + (n1 / NB) * NB * NB, Y + n1 + n1 * ldy,
+                ldy, T);
+  if (e != cudaSuccess) return e;
+  Epilogue ep{};
+  ep.mode = EPI_STORE;  // T = U12 Y22 (n1 x n2, ld n1)
+  ep.Y = T;
+  ep.ldy = n1;
+  e = zgemm_nn(s, n1, n2, n2, U + n1 * ldu, ldu, Y + n1 + n1 * ldy, ldy, ep);
+  if (e != cudaSuccess) return e;
+  Epilogue e2{};
+  e2.mode = EPI_FILTER;  // Y12 = -(Y11 T) (beta = 0: the old Y12 is not read)
+  e2.alpha = -1.0;
+  e2.beta = 0.0;
+  e2.gamma = 0.0;
+  e2.X = Y + n1 * ldy;
+  e2.ldx = ldy;
+  e2.Y = Y + n1 * ldy;
+  e2.ldy = ldy;
+  return zgemm_nn(s, n1, n2, n1, Y, ldy, T, n1, e2);
+}
+
 std::once_flag g_attr_once[kMaxDevices];
 void set_attrs() {
   once_per_device(g_attr_once, []() {
@@ -303,6 +378,26 @@ cudaError_t trsm_right_upper(cudaStream_t s, int64_t m, int64_t n, double2* X, i
   if (m <= 0 || n <= 0) return cudaSuccess;
   const size_t smem = (NB * RP + NB * NB + TK * RP + TK * NB) * sizeof(double2);
   trsm_kernel<<<(unsigned)cdiv(m, RP), FT, smem, s>>>(m, n, X, ldx, U, ldu, dinv, info); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t triangular_inverse(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
+                               const double2* dinv, double2* Y, int64_t ldy, double2* T) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(double2), 0, n * sizeof(double2), n, s);
+  if (e != cudaSuccess) return e;
+  return trinv_rec(s, n, U, ldu, dinv, Y, ldy, T);
+}
+
+cudaError_t max_dev_identity(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
+                             double* out) {
+  dev_identity_kernel<<<1, 1024, 0, s>>>(n, U, ldu, out); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(cudaStream_t s, int64_t n, double2* M, int64_t ldm, bool subtract) {
+  identity_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, M, ldm, subtract);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 // and n - 1 rounds visit every pair once (one sweep).
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "common.cuh"
 
@@ -98,7 +99,10 @@ __global__ void __launch_bounds__(SJ_T)
   const double2* Gb = Gin + (size_t)blockIdx.x * n * n;
   for (int e = t; e < n * n; e += SJ_T) {
     const int r = e % n, c = e / n;
-    G[r + c * SJ_MAX] = Gb[e];
+    // Hermitian part of the input (inputs formed as X^H (G X) are Hermitian
+    // only up to rounding)
+    const double2 a = Gb[e], b = Gb[c + r * n];
+    G[r + c * SJ_MAX] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
     Z[r + c * SJ_MAX] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
@@ -625,7 +629,8 @@ __global__ void oa_lambda_kernel(int64_t n, const double2* __restrict__ S,
 }
 __global__ void oa_e_kernel(int64_t n, const double2* __restrict__ S,
                             const double2* __restrict__ XX, const double* __restrict__ lam,
-                            double2* __restrict__ E, double* __restrict__ partial) {
+                            double2* __restrict__ E, double* __restrict__ partial,
+                            int* __restrict__ pairs, int* __restrict__ npairs) {
   __shared__ double me[256], mc[256];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // row
   const int64_t j = blockIdx.y;                                        // column
@@ -649,6 +654,13 @@ __global__ void oa_e_kernel(int64_t n, const double2* __restrict__ S,
         e = make_double2(0.5 * r.x, 0.5 * r.y);
         emax = 0.5 * sqrt(r.x * r.x + r.y * r.y);
         cmax = sqrt(sv.x * sv.x + sv.y * sv.y);
+        // a pair left to the FP64 finish: recorded (capacity permitting; the
+        // host takes the full FP64 sweeps when the list overflows)
+        const int k = atomicAdd(npairs, 1);
+        if (k < kMaxClusterPairs) {
+          pairs[2 * k] = (int)i;
+          pairs[2 * k + 1] = (int)j;
+        }
       }
     }
     E[i + j * n] = e;
@@ -699,6 +711,48 @@ __global__ void max2_kernel(int64_t nb, const double* __restrict__ partial, doub
     out[1] = c[0];
   }
 }
+// Block S_c = X_c^H (G X_c) of each cluster c of size k (clusters of one size,
+// consecutive in XI / TI): one CTA per cluster, one warp per output entry at a
+// time, lanes over rows, fixed-order reduction. Output k x k column-major.
+__global__ void cluster_gram_kernel(int64_t n, int k, const double2* __restrict__ XI,
+                                    const double2* __restrict__ TI, int64_t ld,
+                                    double2* __restrict__ Sout) {
+  const int c = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double2* X = XI + (int64_t)c * k * ld;
+  const double2* T = TI + (int64_t)c * k * ld;
+  for (int e = warp; e < k * k; e += blockDim.x >> 5) {
+    const int a = e % k, b = e / k;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t r = lane; r < n; r += 32) acc = cadd(acc, cmulc(X[r + a * ld], T[r + b * ld]));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) Sout[(int64_t)c * k * k + a + b * k] = acc;
+  }
+}
+// X(:, idx_c) = XI_c Z_c for each cluster (its FP64 eigenvectors), and the
+// cluster's eigenvalues into lam at the same column indices.
+__global__ void cluster_apply_kernel(int64_t n, int k, const double2* __restrict__ XI, int64_t ld,
+                                     const double2* __restrict__ Z, const double* __restrict__ wz,
+                                     const int* __restrict__ idx, double2* __restrict__ X,
+                                     double* __restrict__ lam) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  const double2* Xc = XI + (int64_t)c * k * ld;
+  const double2* Zc = Z + (int64_t)c * k * k;
+  const int* ic = idx + (int64_t)c * k;
+  if (blockIdx.x == 0 && threadIdx.x < k) lam[ic[threadIdx.x]] = wz[(int64_t)c * k + threadIdx.x];
+  if (r >= n) return;
+  for (int b = 0; b < k; ++b) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < k; ++a) acc = cadd(acc, cmul(Xc[r + a * ld], Zc[a + b * k]));
+    X[r + (int64_t)ic[b] * n] = acc;
+  }
+}
+
 __global__ void rank_vec_kernel(int64_t n, const double* __restrict__ lam, double* w, int* rank) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -777,8 +831,96 @@ cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2
   return cudaGetLastError();
 }
 
+namespace {
+// FP64 finish restricted to the clusters of pairs the refinement left coupled
+// (connected components of the recorded pairs, union-find on the host). For
+// each cluster I: S_I = X_I^H G X_I in FP64, its eigenvectors Z_I by the
+// single-CTA Jacobi kernel, X_I <- X_I Z_I, and its eigenvalues into lam.
+// Returns 1 when done, 0 when not applicable (pair list overflowed, or a
+// cluster larger than the single-CTA kernel), -status on an error.
+int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double2* X,
+                   double2* XI, double* lam, JacobiWork& wk, int* status, int* info) {
+  info[0] = info[1] = 0;
+  int np = 0;
+  if (cudaMemcpyAsync(&np, wk.npairs, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -CHASE_ERR_CUDA;
+  info[1] = np;
+  if (np <= 0 || np > kMaxClusterPairs) return 0;
+  std::vector<int> pr(2 * (size_t)np);
+  if (cudaMemcpy(pr.data(), wk.pairs, pr.size() * sizeof(int), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return -CHASE_ERR_CUDA;
+  std::vector<int> parent((size_t)n);
+  for (int64_t i = 0; i < n; ++i) parent[i] = (int)i;
+  auto find = [&](int x) {
+    while (parent[x] != x) x = parent[x] = parent[parent[x]];
+    return x;
+  };
+  for (int k = 0; k < np; ++k) {
+    const int a = find(pr[2 * k]), b = find(pr[2 * k + 1]);
+    if (a != b) parent[std::max(a, b)] = std::min(a, b);
+  }
+  // members of each component in ascending index order, components by size
+  std::vector<std::vector<int>> comp((size_t)n);
+  for (int64_t i = 0; i < n; ++i) comp[find((int)i)].push_back((int)i);
+  std::vector<int> roots;
+  for (int64_t i = 0; i < n; ++i)
+    if (comp[i].size() >= 2) {
+      info[0] = std::max(info[0], (int)comp[i].size());
+      roots.push_back((int)i);
+    }
+  if (info[0] > SJ_MAX) return 0;
+  if (roots.empty()) return 0;
+  std::stable_sort(roots.begin(), roots.end(),
+                   [&](int a, int b) { return comp[a].size() < comp[b].size(); });
+  std::vector<int> idx;
+  struct Group { int k, count; int64_t off; };
+  std::vector<Group> groups;
+  for (int r : roots) {
+    const int k = (int)comp[r].size();
+    if (groups.empty() || groups.back().k != k) groups.push_back({k, 0, (int64_t)idx.size()});
+    groups.back().count++;
+    idx.insert(idx.end(), comp[r].begin(), comp[r].end());
+  }
+  const int64_t ktot = (int64_t)idx.size();
+  if (cudaMemcpyAsync(wk.cl_idx, idx.data(), ktot * sizeof(int), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
+    return -CHASE_ERR_CUDA;
+  // XI = X(:, idx), TI = G XI (FP64)
+  if (gather_cols(s, n, ktot, X, n, wk.cl_idx, XI, n) != cudaSuccess) return -CHASE_ERR_CUDA;
+  Epilogue ep{};
+  ep.mode = EPI_STORE;
+  ep.Y = wk.T;
+  ep.ldy = n;
+  if (zgemm_nn(s, n, ktot, n, G, ldg, XI, n, ep) != cudaSuccess) return -CHASE_ERR_CUDA;
+  double* wz = reinterpret_cast<double*>(wk.G32b);  // ktot eigenvalues
+  for (const Group& g : groups) {
+    const int64_t off = g.off;
+    cluster_gram_kernel<<<g.count, 256, 0, s>>>(n, g.k, XI + off * n, wk.T + off * n, n, wk.Gw);
+    count_launch();
+    if (jacobi_small_batched(s, g.k, g.count, wk.Gw, wz + off, wk.Gw2, status, wk.max_sweeps) !=
+        cudaSuccess)
+      return -CHASE_ERR_CUDA;
+    cluster_apply_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)g.count, 1), 128, 0, s>>>(
+        n, g.k, XI + off * n, n, wk.Gw2, wz + off, wk.cl_idx + off, X, lam);
+    count_launch();
+  }
+  int hs = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -CHASE_ERR_CUDA;
+  info[1] = (int)roots.size();
+  return hs ? -CHASE_ERR_HEEV_NOCONV : 1;
+}
+}  // namespace
+
 int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double* w, double2* Z,
-                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out) {
+                int64_t ldz, JacobiWork& wk, int* sweeps_out, int* fp64_sweeps_out,
+                int* cluster_out) {
+  if (cluster_out) cluster_out[0] = cluster_out[1] = cluster_out[2] = 0;
   if (n <= 0) return CHASE_OK;
   cudaError_t e;
   int* status = reinterpret_cast<int*>(wk.red + 2 * kCoopMaxGrid + 8);
@@ -850,8 +992,10 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
       return CHASE_ERR_CUDA;
     oa_lambda_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, wk.Gw2, lam); count_launch();
     // E into T (T is free once S is formed)
+    if (cudaMemsetAsync(wk.npairs, 0, sizeof(int), s) != cudaSuccess) return CHASE_ERR_CUDA;
     oa_e_kernel<<<dim3(gb, (unsigned)n, 1), 256, 0, s>>>(n, wk.Gw, wk.Gw2, lam, wk.T,
-                                                        reinterpret_cast<double*>(wk.G32a));
+                                                        reinterpret_cast<double*>(wk.G32a),
+                                                        wk.pairs, wk.npairs);
     count_launch();
     max2_kernel<<<1, 256, 0, s>>>(nb, reinterpret_cast<double*>(wk.G32a), out2); count_launch();
     // Xn = X + X E
@@ -907,7 +1051,23 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   bool conv = emax <= 1e-8 && !tc;
   double2* Zfinal = X;
   double* wsrc = lam;
-  if (!conv || cmax > 1e-14 * gscale) {
+  bool clustered = false;
+  if (conv && cmax > 1e-14 * gscale) {
+    // pairs the refinement could not separate: FP64 Jacobi on each cluster of
+    // them alone (their couplings to every other vector are already at FP64
+    // level); falls through to full FP64 sweeps when the clusters are too many
+    // or too large for the single-CTA kernel
+    int cinfo[2];
+    const int rc = cluster_finish(s, n, G, ldg, X, Xn, lam, wk, status, cinfo);
+    if (rc < 0) return -rc;
+    clustered = rc == 1;
+    if (cluster_out) {
+      cluster_out[0] = clustered ? 1 : 0;  // finished by the cluster path
+      cluster_out[1] = cinfo[0];           // largest cluster
+      cluster_out[2] = cinfo[1];           // clusters (or recorded pairs if not used)
+    }
+  }
+  if (!conv || (cmax > 1e-14 * gscale && !clustered)) {
     // pairs the refinement could not separate (or no convergence): FP64 Jacobi
     // sweeps on G' = X^H G X finish them; eigenvectors X Z'
     Epilogue ep{};
