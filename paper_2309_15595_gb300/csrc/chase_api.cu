@@ -327,7 +327,7 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
   }
   // Alg. 4: a POTRF of the shifted branch failed -> Householder QR of the input
   // (reading: also when the failure is in the CholeskyQR2 after the shift)
-  RC(householder_qr(c->stream, c->N, n, c->W, c->N, X, ldx, c->hw, c->gram_ws, c->gram_ws_elems));
+  RC(householder_qr(c->stream, c->N, n, c->W, c->N, X, ldx, c->hw));
   if (variant) *variant = CHASE_QR_HOUSEHOLDER;
   return CHASE_OK;
 }

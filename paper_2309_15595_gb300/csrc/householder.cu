@@ -244,20 +244,26 @@ cudaError_t householder_alloc(HouseholderWork& w, int64_t N, int64_t ne) {
   if ((e = cudaMalloc(&w.tau, (size_t)ne * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.scale, 2 * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.bad, sizeof(int))) != cudaSuccess) return e;
+  // the Gram products here have NB rows and up to max(NB, ne) columns
+  w.gws_elems = gram_workspace_elems(NBH, std::max<int64_t>(NBH, ne));
+  if ((e = cudaMalloc(&w.gws, w.gws_elems * sizeof(double2))) != cudaSuccess) return e;
   w.N = N;
   w.ne = ne;
   return cudaSuccess;
 }
 
 void householder_free(HouseholderWork& w) {
-  void* bufs[] = {w.Vp, w.T, w.S, w.W, w.W2, w.dots, w.norms, w.beta, w.tau, w.scale, w.bad};
+  void* bufs[] = {w.Vp, w.T, w.S, w.W, w.W2, w.dots, w.norms, w.beta, w.tau, w.scale, w.bad,
+                  w.gws};
   for (void* b : bufs)
     if (b) cudaFree(b);
   w = HouseholderWork{};
 }
 
 int householder_qr(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx, double2* Q,
-                   int64_t ldq, HouseholderWork& w, double2* gram_ws, size_t gram_ws_elems) {
+                   int64_t ldq, HouseholderWork& w) {
+  double2* const gram_ws = w.gws;
+  const size_t gram_ws_elems = w.gws_elems;
   if (n <= 0) return CHASE_OK;
   if (m < n || m > w.N || n > w.ne) return CHASE_ERR_INVALID_ARG;
 #define HK(call)                                     \

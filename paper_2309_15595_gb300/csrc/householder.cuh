@@ -19,6 +19,8 @@ struct HouseholderWork {
   double2* tau = nullptr;    // reflector coefficients
   double2* scale = nullptr;  // 1 / (alpha - beta) of the current column
   int* bad = nullptr;        // a non-finite reflector was met
+  double2* gws = nullptr;    // split-K workspace of the NB-row Gram products
+  size_t gws_elems = 0;
   int64_t N = 0, ne = 0;
 };
 
@@ -26,9 +28,8 @@ cudaError_t householder_alloc(HouseholderWork& w, int64_t N, int64_t ne);
 void householder_free(HouseholderWork& w);
 // X (m x n, ldx; m >= n) is overwritten by the reflectors and R; Q (m x n, ldq,
 // not aliasing X) receives the orthonormal factor with diag(R) real positive.
-// gram_ws: workspace of zgram. Synchronises; CHASE_ERR_QR_BREAKDOWN if the input
-// held non-finite values.
+// Synchronises; CHASE_ERR_QR_BREAKDOWN if the input held non-finite values.
 int householder_qr(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx, double2* Q,
-                   int64_t ldq, HouseholderWork& w, double2* gram_ws, size_t gram_ws_elems);
+                   int64_t ldq, HouseholderWork& w);
 
 }  // namespace chase

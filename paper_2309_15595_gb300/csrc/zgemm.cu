@@ -326,6 +326,7 @@ cudaError_t zgram(cudaStream_t s, int64_t K, int64_t m, int64_t n, const double2
                   const double2* Y, int64_t ldy, double2* G, int64_t ldg, bool hermitian,
                   double2* ws, size_t ws_elems) {
   if (m <= 0 || n <= 0) return cudaSuccess;
+  if (ws_elems < (size_t)m * n) return cudaErrorInvalidValue;  // no room for one partial
   const int64_t tm = cdiv(m, BM), tn = cdiv(n, BN);
   const int64_t tiles = hermitian ? tm * (tm + 1) / 2 : tm * tn;
   int64_t splits = cdiv(3 * num_sms(), tiles);
