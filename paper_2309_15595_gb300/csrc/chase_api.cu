@@ -222,30 +222,30 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 //
 // With the tensor-core FP64 products (fp64_tensor):
 //  * Gram matrix. A digit-sliced X^H X has an error of about sqrt(N) 2^-47 of
-//    the column maxima (FP64: sqrt(N) 2^-53); the orthogonality a pass delivers
-//    is about kappa(X)^2 times the Gram error. A pass that is not the last of
-//    its variant (its error is removed by the next pass) and the last pass of
-//    CholeskyQR2 / shifted CholeskyQR2 (whose input is already orthonormal to
-//    about the previous pass's kappa^2 u) use the tensor cores; CholeskyQR1's
-//    single pass (kappa up to 20) keeps the FP64 CUDA-core Gram. A last pass
-//    whose U turns out not to be near the identity (max |U - I| > 1e-3, so the
-//    input was not near-orthonormal) recomputes its Gram in FP64 before using it.
-//  * X U^-1. When max |U - I| <= 1e-3, X U^-1 = X + X D with D = U^-1 - I
-//    (|D| ~ 1e-3 or less): the digit-sliced product X D then carries an error of
-//    about sqrt(n) 2^-46 |X| |D|, below 1e-15 of |X|, so it runs on the tensor
-//    cores (U^-1 by a recursive blocked inversion with FP64 GEMMs). Otherwise
+//    the product of the two columns' largest entries (FP64: sqrt(N) 2^-53 of the
+//    column norms' product). For the localised columns of nearly converged Ritz
+//    vectors (one entry near 1, the rest small) that is 1e-12 - 1e-11 of the
+//    column norms, and the orthogonality a pass delivers is the Gram error
+//    times kappa(X)^2. So only passes that are not the last of their variant
+//    (the next pass removes their error) use the tensor cores; every variant's
+//    last pass keeps the FP64 CUDA-core Gram.
+//  * X U^-1. When max |U - I| <= 1e-4 (the input is orthonormal to about 1e-4),
+//    X U^-1 = X + X D with D = U^-1 - I, |D| <= ~1e-4: the digit-sliced product
+//    X D carries an error of about sqrt(2n) 2^-44 max|X_i.| max|D_.j|, below
+//    1e-15 absolute, so it runs on the tensor cores (U^-1 by a recursive blocked
+//    inversion with FP64 GEMMs). Otherwise
 //    X U^-1 is the FP64 triangular solve: a digit-sliced product with a general
 //    U^-1, whose columns mix entries of very different size for a filtered
 //    block, would keep the small entries only to 2^-48 of their column's
 //    largest and lose the span of the small columns.
-constexpr double kNearIdentity = 1e-3;
+constexpr double kNearIdentity = 1e-4;
 
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
-                bool tc_gram, bool last, int* info_h) {
+                bool last, int* info_h) {
   const bool tensor = c->p.fp64_tensor != 0;
-  bool tc = tensor && tc_gram;
+  const bool tc = tensor && !last;
   double* dev_h = c->host + 2 * c->ne + 10;
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  {
     if (tc) {
       Epilogue ep{};
       ep.mode = EPI_STORE;
@@ -266,12 +266,6 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
     CK(cudaStreamSynchronize(c->stream));
     if (tc) RC(ozaki_check(c->stream, c->ow));
     if (*info_h != 0) return CHASE_OK;
-    // a last pass whose input was not near-orthonormal: FP64 Gram after all
-    if (tc && last && !(*dev_h <= kNearIdentity)) {
-      tc = false;
-      continue;
-    }
-    break;
   }
   if (tensor && *dev_h <= kNearIdentity) {
     // X <- X + X (U^-1 - I) on the tensor cores; U^-1 (recursive blocked
@@ -304,8 +298,7 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
     const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
     bool ok = true;
     for (int k = 0; k < passes && ok; ++k) {
-      // CholeskyQR1's single pass keeps the FP64 Gram (see cholqr_pass)
-      RC(cholqr_pass(c, X, ldx, n, 0.0, passes == 2, k == passes - 1, info_h));
+      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, info_h));
       ok = (*info_h == 0);
     }
     if (ok) {
@@ -318,9 +311,9 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
   }
   // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2, then CholeskyQR2
   const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
-  RC(cholqr_pass(c, X, ldx, n, factor, true, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, true, info_h));
+  RC(cholqr_pass(c, X, ldx, n, factor, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, info_h));
   if (*info_h == 0) {
     if (variant) *variant = CHASE_QR_SHIFTED;
     return CHASE_OK;

@@ -23,6 +23,11 @@ namespace {
     const int _rc = (call);         \
     if (_rc != CHASE_OK) return _rc; \
   } while (0)
+#define RC_NEG(call)                  \
+  do {                                \
+    const int _rc = (call);           \
+    if (_rc != CHASE_OK) return -_rc; \
+  } while (0)
 
 constexpr int kMaxSweeps = 40;
 constexpr int kCoopMaxGrid = 2048;  // reduction scratch holds 2 * kCoopMaxGrid partials
@@ -753,6 +758,17 @@ __global__ void cluster_apply_kernel(int64_t n, int k, const double2* __restrict
   }
 }
 
+// X(:, idx[j]) = P(:, j) and lam[idx[j]] = Re S(j, j) for a large cluster's
+// eigenvectors P (n x m, ld n) and its diagonalised block S (m x m, ld m).
+__global__ void scatter_cluster_kernel(int64_t n, int64_t m, const double2* __restrict__ P,
+                                       const int* __restrict__ idx, const double2* __restrict__ S,
+                                       double2* __restrict__ X, double* __restrict__ lam) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) lam[idx[j]] = S[j + j * m].x;
+  if (r < n) X[r + (int64_t)idx[j] * n] = P[r + j * n];
+}
+
 __global__ void rank_vec_kernel(int64_t n, const double* __restrict__ lam, double* w, int* rank) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -834,13 +850,19 @@ cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2
 namespace {
 // FP64 finish restricted to the clusters of pairs the refinement left coupled
 // (connected components of the recorded pairs, union-find on the host). For
-// each cluster I: S_I = X_I^H G X_I in FP64, its eigenvectors Z_I by the
-// single-CTA Jacobi kernel, X_I <- X_I Z_I, and its eigenvalues into lam.
+// each cluster I: S_I = X_I^H G X_I in FP64, its eigenvectors Z_I by Jacobi
+// (clusters of up to 64 batched in the single-CTA kernel, larger ones one by
+// one in the cooperative kernel on their m x m block), X_I <- X_I Z_I, and its
+// eigenvalues into lam. A cluster's coupling to every other vector is already
+// at FP64 rounding level after the refinement, so the blocks are independent.
 // Returns 1 when done, 0 when not applicable (pair list overflowed, or a
-// cluster larger than the single-CTA kernel), -status on an error.
+// cluster above 0.7 n, where the full FP64 sweeps cost about the same),
+// -status on an error. *sweeps64 receives the FP64 sweeps of the large clusters.
 int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double2* X,
-                   double2* XI, double* lam, JacobiWork& wk, int* status, int* info) {
+                   double2* XI, double* lam, JacobiWork& wk, int* status, int* info,
+                   int max_sweeps, int* sweeps64) {
   info[0] = info[1] = 0;
+  *sweeps64 = 0;
   int np = 0;
   if (cudaMemcpyAsync(&np, wk.npairs, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -870,7 +892,8 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
       info[0] = std::max(info[0], (int)comp[i].size());
       roots.push_back((int)i);
     }
-  if (info[0] > SJ_MAX) return 0;
+  // a large cluster's Jacobi rotations (m x m, ld m) live in G32a viewed as FP64
+  if ((double)info[0] > 0.7 * (double)n) return 0;
   if (roots.empty()) return 0;
   std::stable_sort(roots.begin(), roots.end(),
                    [&](int a, int b) { return comp[a].size() < comp[b].size(); });
@@ -898,6 +921,33 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
   double* wz = reinterpret_cast<double*>(wk.G32b);  // ktot eigenvalues
   for (const Group& g : groups) {
     const int64_t off = g.off;
+    if (g.k > SJ_MAX) {  // one large cluster at a time, FP64 cooperative Jacobi
+      for (int q = 0; q < g.count; ++q) {
+        const int64_t m = g.k, o = off + (int64_t)q * m;
+        if (zgram(s, n, m, m, XI + o * n, n, wk.T + o * n, n, wk.Gw, m, false, wk.gram_ws,
+                  wk.gram_ws_elems) != cudaSuccess ||
+            hermitian_part(s, m, wk.Gw, m) != cudaSuccess)
+          return -CHASE_ERR_CUDA;
+        double2* Zr = reinterpret_cast<double2*>(wk.G32a);
+        identity_kernel<<<dim3((unsigned)cdiv(m, 128), (unsigned)m, 1), 128, 0, s>>>(m, Zr);
+        count_launch();
+        int sw = 0;
+        bool conv = false, in_g1 = false;
+        RC_NEG(run_coop<double>(s, m, wk.Gw, wk.Gw2, Zr, wz + n, wk.red, max_sweeps, 1e-15, 1e-12,
+                                &sw, &conv, &in_g1));
+        *sweeps64 += sw;
+        if (!conv) return -CHASE_ERR_HEEV_NOCONV;
+        Epilogue ez{};
+        ez.mode = EPI_STORE;  // P = X_I Z into the cluster's (now free) columns of T
+        ez.Y = wk.T + o * n;
+        ez.ldy = n;
+        if (zgemm_nn(s, n, m, m, XI + o * n, n, Zr, m, ez) != cudaSuccess) return -CHASE_ERR_CUDA;
+        scatter_cluster_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)m, 1), 128, 0, s>>>(
+            n, m, wk.T + o * n, wk.cl_idx + o, in_g1 ? wk.Gw2 : wk.Gw, X, lam);
+        count_launch();
+      }
+      continue;
+    }
     cluster_gram_kernel<<<g.count, 256, 0, s>>>(n, g.k, XI + off * n, wk.T + off * n, n, wk.Gw);
     count_launch();
     if (jacobi_small_batched(s, g.k, g.count, wk.Gw, wz + off, wk.Gw2, status, wk.max_sweeps) !=
@@ -1058,7 +1108,8 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     // level); falls through to full FP64 sweeps when the clusters are too many
     // or too large for the single-CTA kernel
     int cinfo[2];
-    const int rc = cluster_finish(s, n, G, ldg, X, Xn, lam, wk, status, cinfo);
+    const int rc = cluster_finish(s, n, G, ldg, X, Xn, lam, wk, status, cinfo, cap(kMaxSweeps),
+                                  &sw64);
     if (rc < 0) return -rc;
     clustered = rc == 1;
     if (cluster_out) {
