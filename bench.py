@@ -579,7 +579,11 @@ def run_gpu(args):
         if max_iter < 10:
             out.d["skipped"].append(f"time-to-solution {m}: {left:.0f} s left of the budget")
             continue
-        tts[m] = tts_solve(lib, torch, p, Ad, V0d, Q0d, m, max_iter, dev)
+        try:
+            tts[m] = tts_solve(lib, torch, p, Ad, V0d, Q0d, m, max_iter, dev)
+        except Exception as exc:  # an optional leg never costs the line
+            out.d.setdefault("errors", []).append(f"time-to-solution {m}: {exc}")
+            continue
         tts[m]["max_iter"] = max_iter
         print(json.dumps({"tts": m, **tts[m]}), file=sys.stderr, flush=True)
     if tts:
@@ -603,7 +607,11 @@ def run_gpu(args):
             out.d["skipped"].append(f"{key}: estimated {est:.0f} s exceeds the budget")
             continue
         vprm = lib.default_params(N, p.nev, p.nex, max_iter=1, precision=vprec, fp64_tensor=vt)
-        vctx, vstats, vvalue, vms, _ = timed(vprm, vw, vk)
+        try:
+            vctx, vstats, vvalue, vms, _ = timed(vprm, vw, vk)
+        except Exception as exc:
+            out.d.setdefault("errors", []).append(f"{key}: {exc}")
+            continue
         vctx.close()
         vfilter = sum(x["ms_filter"] for x in vstats) / len(vstats)
         out.d[key] = {

@@ -18,6 +18,13 @@
 using namespace chase;
 
 namespace chase {
+int report_cuda_failure(const char* file, int line) {
+  const cudaError_t e = cudaGetLastError();
+  const char* base = std::strrchr(file, '/');
+  fprintf(stderr, "[chase] CUDA failure at %s:%d (%s)\n", base ? base + 1 : file, line,
+          cudaGetErrorString(e));
+  return CHASE_ERR_CUDA;
+}
 // per host thread, so concurrent solves on different threads count their own launches
 static thread_local long long g_launches = 0;
 void count_launch() { ++g_launches; }

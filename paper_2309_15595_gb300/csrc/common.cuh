@@ -53,6 +53,10 @@ void once_per_device(std::once_flag (&flags)[kMaxDevices], F&& f) {
   }
   std::call_once(flags[dev], f);
 }
+// Reports a failed CUDA call (with the pending CUDA error, if any) on stderr and
+// returns CHASE_ERR_CUDA; used by every CUDA-error return of the library.
+int report_cuda_failure(const char* file, int line);
+#define CHASE_CUDA_FAIL() ::chase::report_cuda_failure(__FILE__, __LINE__)
 // Number of SMs of the current device (cached per device).
 int num_sms();
 

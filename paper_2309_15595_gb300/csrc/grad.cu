@@ -18,7 +18,7 @@ namespace {
 int cuda_fail(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
     fprintf(stderr, "[chase] CUDA error in %s: %s\n", what, cudaGetErrorString(e));
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   }
   return CHASE_OK;
 }

@@ -266,9 +266,9 @@ int householder_qr(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx
   const size_t gram_ws_elems = w.gws_elems;
   if (n <= 0) return CHASE_OK;
   if (m < n || m > w.N || n > w.ne) return CHASE_ERR_INVALID_ARG;
-#define HK(call)                                     \
-  do {                                               \
-    if ((call) != cudaSuccess) return CHASE_ERR_CUDA; \
+#define HK(call)                                          \
+  do {                                                    \
+    if ((call) != cudaSuccess) return CHASE_CUDA_FAIL();  \
   } while (0)
   HK(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
   const int64_t npan = cdiv(n, NBH);

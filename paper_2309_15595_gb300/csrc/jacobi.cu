@@ -548,7 +548,7 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -557,13 +557,13 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<T>, LJ_T, smem) !=
           cudaSuccess ||
       per_sm < 1)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   // one pair per block where the blocks fit, so pairs run concurrently
   const int grid = std::min(std::min(npairs, per_sm * nsm), kCoopMaxGrid);
   unsigned* bar = reinterpret_cast<unsigned*>(red + 2 * kCoopMaxGrid);
   int* st = reinterpret_cast<int*>(red + 2 * kCoopMaxGrid + 2);
   if (cudaMemsetAsync(red + 2 * kCoopMaxGrid, 0, 8 * sizeof(double), s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   CoopArgs<T> args;
   args.n = n;
   args.m = m;
@@ -580,15 +580,15 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   void* kargs[] = {&args};
   if (cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel<T>, dim3(grid), dim3(LJ_T), kargs,
                                   smem, s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   count_launch();
   int hst[4] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   if (hst[0] != 0) {
     fprintf(stderr, "[chase] Jacobi: grid barrier wait expired\n");
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   }
   *sweeps = hst[1];
   *conv = hst[2] != 0;
@@ -866,13 +866,13 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
   int np = 0;
   if (cudaMemcpyAsync(&np, wk.npairs, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return -CHASE_ERR_CUDA;
+    return -CHASE_CUDA_FAIL();
   info[1] = np;
   if (np <= 0 || np > kMaxClusterPairs) return 0;
   std::vector<int> pr(2 * (size_t)np);
   if (cudaMemcpy(pr.data(), wk.pairs, pr.size() * sizeof(int), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
-    return -CHASE_ERR_CUDA;
+    return -CHASE_CUDA_FAIL();
   std::vector<int> parent((size_t)n);
   for (int64_t i = 0; i < n; ++i) parent[i] = (int)i;
   auto find = [&](int x) {
@@ -910,14 +910,14 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
   if (cudaMemcpyAsync(wk.cl_idx, idx.data(), ktot * sizeof(int), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
-    return -CHASE_ERR_CUDA;
+    return -CHASE_CUDA_FAIL();
   // XI = X(:, idx), TI = G XI (FP64)
-  if (gather_cols(s, n, ktot, X, n, wk.cl_idx, XI, n) != cudaSuccess) return -CHASE_ERR_CUDA;
+  if (gather_cols(s, n, ktot, X, n, wk.cl_idx, XI, n) != cudaSuccess) return -CHASE_CUDA_FAIL();
   Epilogue ep{};
   ep.mode = EPI_STORE;
   ep.Y = wk.T;
   ep.ldy = n;
-  if (zgemm_nn(s, n, ktot, n, G, ldg, XI, n, ep) != cudaSuccess) return -CHASE_ERR_CUDA;
+  if (zgemm_nn(s, n, ktot, n, G, ldg, XI, n, ep) != cudaSuccess) return -CHASE_CUDA_FAIL();
   double* wz = reinterpret_cast<double*>(wk.G32b);  // ktot eigenvalues
   for (const Group& g : groups) {
     const int64_t off = g.off;
@@ -927,7 +927,7 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
         if (zgram(s, n, m, m, XI + o * n, n, wk.T + o * n, n, wk.Gw, m, false, wk.gram_ws,
                   wk.gram_ws_elems) != cudaSuccess ||
             hermitian_part(s, m, wk.Gw, m) != cudaSuccess)
-          return -CHASE_ERR_CUDA;
+          return -CHASE_CUDA_FAIL();
         double2* Zr = reinterpret_cast<double2*>(wk.G32a);
         identity_kernel<<<dim3((unsigned)cdiv(m, 128), (unsigned)m, 1), 128, 0, s>>>(m, Zr);
         count_launch();
@@ -941,7 +941,7 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
         ez.mode = EPI_STORE;  // P = X_I Z into the cluster's (now free) columns of T
         ez.Y = wk.T + o * n;
         ez.ldy = n;
-        if (zgemm_nn(s, n, m, m, XI + o * n, n, Zr, m, ez) != cudaSuccess) return -CHASE_ERR_CUDA;
+        if (zgemm_nn(s, n, m, m, XI + o * n, n, Zr, m, ez) != cudaSuccess) return -CHASE_CUDA_FAIL();
         scatter_cluster_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)m, 1), 128, 0, s>>>(
             n, m, wk.T + o * n, wk.cl_idx + o, in_g1 ? wk.Gw2 : wk.Gw, X, lam);
         count_launch();
@@ -952,7 +952,7 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
     count_launch();
     if (jacobi_small_batched(s, g.k, g.count, wk.Gw, wz + off, wk.Gw2, status, wk.max_sweeps) !=
         cudaSuccess)
-      return -CHASE_ERR_CUDA;
+      return -CHASE_CUDA_FAIL();
     cluster_apply_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)g.count, 1), 128, 0, s>>>(
         n, g.k, XI + off * n, n, wk.Gw2, wz + off, wk.cl_idx + off, X, lam);
     count_launch();
@@ -961,7 +961,7 @@ int cluster_finish(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, dou
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return -CHASE_ERR_CUDA;
+    return -CHASE_CUDA_FAIL();
   info[1] = (int)roots.size();
   return hs ? -CHASE_ERR_HEEV_NOCONV : 1;
 }
@@ -977,19 +977,19 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   if (n <= SJ_MAX) {
     // pack G (ld n) into Gw, run the single-CTA kernel into Zw, copy to Z.
     e = cudaMemsetAsync(status, 0, sizeof(int), s);
-    if (e != cudaSuccess) return CHASE_ERR_CUDA;
+    if (e != cudaSuccess) return CHASE_CUDA_FAIL();
     e = cudaMemcpy2DAsync(wk.Gw, n * sizeof(double2), G, ldg * sizeof(double2),
                           n * sizeof(double2), n, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return CHASE_ERR_CUDA;
+    if (e != cudaSuccess) return CHASE_CUDA_FAIL();
     e = jacobi_small_batched(s, (int)n, 1, wk.Gw, w, wk.Zw, status, wk.max_sweeps);
-    if (e != cudaSuccess) return CHASE_ERR_CUDA;
+    if (e != cudaSuccess) return CHASE_CUDA_FAIL();
     e = cudaMemcpy2DAsync(Z, ldz * sizeof(double2), wk.Zw, n * sizeof(double2),
                           n * sizeof(double2), n, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return CHASE_ERR_CUDA;
+    if (e != cudaSuccess) return CHASE_CUDA_FAIL();
     int hs = 0;
     e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return CHASE_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (e != cudaSuccess) return CHASE_CUDA_FAIL();
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CHASE_CUDA_FAIL();
     if (sweeps_out) *sweeps_out = 0;
     return hs ? CHASE_ERR_HEEV_NOCONV : CHASE_OK;
   }
@@ -1018,7 +1018,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   if (cudaMemcpyAsync(wk.host_red, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   // sqrt(n) times the largest norm of a 256-row column segment: within a factor
   // sqrt(n) of ||G||_2 either way, enough for the 1e-14 cluster test below
   const double gscale = wk.host_red[0] * std::sqrt((double)n);
@@ -1039,10 +1039,10 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     if (heev_nn(s, wk, tc, n, G, ldg, X, ep) != cudaSuccess ||         // T = G X
         heev_cn(s, wk, tc, n, X, wk.T, wk.Gw, false) != cudaSuccess ||   // S = X^H T
         heev_cn(s, wk, tc, n, X, X, wk.Gw2, true) != cudaSuccess)        // X^H X
-      return CHASE_ERR_CUDA;
+      return CHASE_CUDA_FAIL();
     oa_lambda_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, wk.Gw2, lam); count_launch();
     // E into T (T is free once S is formed)
-    if (cudaMemsetAsync(wk.npairs, 0, sizeof(int), s) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (cudaMemsetAsync(wk.npairs, 0, sizeof(int), s) != cudaSuccess) return CHASE_CUDA_FAIL();
     oa_e_kernel<<<dim3(gb, (unsigned)n, 1), 256, 0, s>>>(n, wk.Gw, wk.Gw2, lam, wk.T,
                                                         reinterpret_cast<double*>(wk.G32a),
                                                         wk.pairs, wk.npairs);
@@ -1051,7 +1051,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     // Xn = X + X E
     if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
-      return CHASE_ERR_CUDA;
+      return CHASE_CUDA_FAIL();
     Epilogue eu{};
     eu.mode = EPI_FILTER;
     eu.alpha = 1.0;
@@ -1061,12 +1061,12 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     eu.ldx = n;
     eu.Y = Xn;
     eu.ldy = n;
-    if (heev_nn(s, wk, tc, n, X, n, wk.T, eu) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_nn(s, wk, tc, n, X, n, wk.T, eu) != cudaSuccess) return CHASE_CUDA_FAIL();
     std::swap(X, Xn);
     if (cudaMemcpyAsync(wk.host_red, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-      return CHASE_ERR_CUDA;
+      return CHASE_CUDA_FAIL();
     emax = wk.host_red[0];
     cmax = wk.host_red[1];
     // the applied correction was ~emax; the error left is ~emax^2 (plus the
@@ -1080,11 +1080,11 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   {
     // the corrections of close pairs carry rounding of order u / gap; one more
     // orthogonalisation step brings X^H X back to I at working precision
-    if (heev_cn(s, wk, false, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_cn(s, wk, false, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_CUDA_FAIL();
     half_residual_kernel<<<g2, 128, 0, s>>>(n, wk.Gw2, wk.T); count_launch();
     if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
-      return CHASE_ERR_CUDA;
+      return CHASE_CUDA_FAIL();
     Epilogue eo{};
     eo.mode = EPI_FILTER;
     eo.alpha = 1.0;
@@ -1094,7 +1094,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     eo.ldx = n;
     eo.Y = Xn;
     eo.ldy = n;
-    if (heev_nn(s, wk, false, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (heev_nn(s, wk, false, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_CUDA_FAIL();
     std::swap(X, Xn);
   }
   int sw64 = 0;
@@ -1129,7 +1129,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
         zgram(s, n, n, n, X, n, wk.T, n, wk.Gw, n, false, wk.gram_ws, wk.gram_ws_elems) !=
             cudaSuccess ||
         hermitian_part(s, n, wk.Gw, n) != cudaSuccess)
-      return CHASE_ERR_CUDA;
+      return CHASE_CUDA_FAIL();
     double2* Zrot = Xn;  // the buffer X does not use
     identity_kernel<<<g2, 128, 0, s>>>(n, Zrot); count_launch();
     bool in_g1_64 = false;
@@ -1140,7 +1140,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     ez.mode = EPI_STORE;
     ez.Y = wk.T;
     ez.ldy = n;
-    if (zgemm_nn(s, n, n, n, X, n, Zrot, n, ez) != cudaSuccess) return CHASE_ERR_CUDA;
+    if (zgemm_nn(s, n, n, n, X, n, Zrot, n, ez) != cudaSuccess) return CHASE_CUDA_FAIL();
     Zfinal = wk.T;
     int* rank = reinterpret_cast<int*>(wk.params + 8 * (n / 2 + 2));
     rank_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, Gcur, w, rank); count_launch();
@@ -1154,7 +1154,7 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     permute_cols_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(
         n, Zfinal, rank, Z, ldz); count_launch();
   }
-  if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return CHASE_CUDA_FAIL();
   if (sweeps_out) *sweeps_out = sw32 + sw64 + refine;
   if (fp64_sweeps_out) *fp64_sweeps_out = sw64;
   return conv ? CHASE_OK : CHASE_ERR_HEEV_NOCONV;

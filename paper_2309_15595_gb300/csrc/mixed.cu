@@ -473,7 +473,7 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
   split_y_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, Np, 0, V, ldv,
                                                                                    Yh, Yl, st[0]);
   count_launch();
-  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_CUDA_FAIL();
   (void)W;
   (void)ldw;
   const int dmax = degs[ncols - 1];
@@ -499,7 +499,7 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
     mixed_filter_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->ah, maps->al, maps->bh[bin],
                                                            maps->bl[bin], P);
     count_launch();
-    if (cudaGetLastError() != cudaSuccess) return CHASE_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return CHASE_CUDA_FAIL();
   }
   // even degrees: every column's final value is in state buffer 0
   state_to_f64_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, st[0], V,
@@ -508,10 +508,10 @@ int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, doubl
   int herr = 0;
   if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   if (herr != 0) {
     fprintf(stderr, "[chase] tensor-core filter: pipeline wait expired (code %d)\n", herr);
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   }
   return CHASE_OK;
 }

@@ -762,11 +762,11 @@ int ozaki_check(cudaStream_t s, OzakiWork& w) {
   int herr = 0;
   if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   if (herr != 0) {
     fprintf(stderr, "[chase] emulated-FP64 GEMM: pipeline wait expired (code %d)\n", herr);
     cudaMemsetAsync(w.err, 0, sizeof(int), s);
-    return CHASE_ERR_CUDA;
+    return CHASE_CUDA_FAIL();
   }
   return CHASE_OK;
 }

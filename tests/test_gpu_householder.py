@@ -14,9 +14,10 @@ fails. Two kinds of input:
 * Nearly dependent: the first `nwell` columns well conditioned, the others
   combinations of them plus new directions of relative size 1e-18
   (kappa ~ 1e16). Whether a POTRF after the shift meets a non-positive pivot
-  then depends on rounding, so the test requires the same Alg. 4 branch as the
-  oracle on the same machine and, on the Householder branch, the leading
-  columns element by element.
+  then depends on rounding (the oracle takes either branch depending on the
+  machine's BLAS), so the test does not compare branches: whichever branch the
+  GPU takes must give an orthonormal, backward-stable Q whose leading `nwell`
+  columns (unique there) match the oracle's element by element.
 
 Checks on every case: orthonormality ||Q^H Q - I|| <= 1e-12; backward error
 ||X - Q Q^H X|| <= 1e-13 ||X|| (Householder QR is backward stable); diag(R)
@@ -89,7 +90,7 @@ def test_householder_fallback_nearly_dependent(lib, m, n, nwell, seed, tensor):
     X = nearly_dependent(m, n, nwell, seed)
     Qo, vo, info = O.caqr(X, 1e20)
     v, Q = _run(lib, X, n, 1e20, tensor)
-    assert v == vo  # the same Alg. 4 branch as the oracle on this machine
+    assert v in (lib.CHASE_QR_SHIFTED, lib.CHASE_QR_HOUSEHOLDER)
     orth, back = _common_checks(X, Q, n, nwell)
     lead = np.abs(Q[:, :nwell] - Qo[:, :nwell]).max()
     print(f"nearly dependent m={m} n={n}: variant {v} orth {orth:.2e} backward {back:.2e} "
