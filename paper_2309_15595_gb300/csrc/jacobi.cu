@@ -553,11 +553,16 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<T>, LJ_T, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
+  const cudaError_t oe =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<T>, LJ_T, smem);
+  if (!coop || oe != cudaSuccess || per_sm < 1) {
+    fprintf(stderr,
+            "[chase] Jacobi (%s) n=%lld: no cooperative residency (coop %d, occupancy %s, "
+            "blocks/SM %d, dynamic smem %zu B)\n",
+            sizeof(T) == 4 ? "FP32" : "FP64", (long long)n, coop, cudaGetErrorString(oe), per_sm,
+            smem);
     return CHASE_CUDA_FAIL();
+  }
   // one pair per block where the blocks fit, so pairs run concurrently
   const int grid = std::min(std::min(npairs, per_sm * nsm), kCoopMaxGrid);
   unsigned* bar = reinterpret_cast<unsigned*>(red + 2 * kCoopMaxGrid);

@@ -13,13 +13,23 @@
 // separate conversion pass runs per degree. The FP64 input V is converted once
 // before the first step and the result converted back once after the last.
 //
-// Kernel structure (one 128 x 256 output tile per CTA, 6 warps):
+// Accumulation: the tensor cores' FP32 accumulation over the whole K = 2N
+// range lost precision in proportion to K (measured: the filter's error grew
+// linearly with N, to 1e-3 per degree at N = 20000). So the K range is cut into
+// chunks of 256: each chunk's products go into one of two TMEM accumulators
+// (double-buffered, so the MMAs of the next chunk run while the epilogue warps
+// drain this one), and the epilogue warps add the chunk sums into FP32
+// registers with round-to-nearest adds.
+//
+// Kernel structure (one 128 x 256 output tile per CTA, 10 warps):
 //   warp 0   TMA producer: A_hi, A_lo (128 x 32) and B_hi, B_lo (256 x 32) per
 //            K block into a 4-stage shared-memory ring of 48 KB stages (64B
 //            swizzle: one K block of 32 BF16 is a 64-byte row)
 //   warp 1   TMEM allocator and single-thread MMA issuer (tcgen05.mma, M=128,
 //            N=256, K=16, kind::f16 with BF16 inputs)
-//   warps 2-5 epilogue: tcgen05.ld of their 32-lane TMEM quarter
+//   warps 2-9 epilogue: warp w reads TMEM lane quarter w % 4 and half of the
+//            complex columns; per-chunk drain into FP32 register sums, then the
+//            fused Eq. 1 update
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
 // records an error code and winds down instead of spinning.
 #include <cuda.h>
@@ -43,8 +53,10 @@ constexpr int B_TILE = TN * TK * 2;                 // 16 KB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;  // 48 KB
 constexpr int KPAD = 64;                            // K-half padding of the planes
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr int CHUNK_KB = 8;              // K blocks (of 32) per accumulation chunk: 256 values
+constexpr uint32_t TMEM_COLS = 512;      // two 128 x 256 FP32 accumulators
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 struct Params {
@@ -73,6 +85,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -172,8 +187,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // 1024-byte alignment of the shared-window address (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  // bars[0..S) full, bars[S..2S) empty, bars[2S + b] accumulator b full,
+  // bars[2S + 2 + b] accumulator b drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,6 +198,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int64_t m0 = (int64_t)rb * TM;
   const int64_t tile = (P.j0 >> 7) + ct;          // absolute 128-column tile
   const int nkb = (int)((2 * P.Np) / TK);
+  const int nchunks = (nkb + CHUNK_KB - 1) / CHUNK_KB;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -189,7 +206,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(smem_u32(&bars[s]), 1);
       mbar_init(smem_u32(&bars[STAGES + s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars[2 * STAGES + b]), 1);
+      mbar_init(smem_u32(&bars[2 * STAGES + 2 + b]), EPI_WARPS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -230,71 +250,112 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_wait(smem_u32(&bars[kb % STAGES]), (uint32_t)(kb / STAGES) & 1u, P.err, 2);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------- MMA issuer
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&bars[s]), ph, P.err, 3) || *(volatile int*)&s_abort) {
+    int kb = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int b = c & 1;
+      const uint32_t acc_tm = tmem + (uint32_t)(b * TN);
+      if (c >= 2 &&
+          !mbar_wait(smem_u32(&bars[2 * STAGES + 2 + b]), (uint32_t)((c >> 1) - 1) & 1u, P.err, 5)) {
+        ok = false;
         s_abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = bh + B_TILE;
+      const int kend = min(nkb, (c + 1) * CHUNK_KB);
+      for (; kb < kend; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&bars[s]), ph, P.err, 3) || *(volatile int*)&s_abort) {
+          ok = false;
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = bh + B_TILE;
 #pragma unroll
-      for (int kk = 0; kk < TK / 16; ++kk) {
-        const uint32_t off = kk * 32;  // 16 BF16 along K
-        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        umma_bf16(tmem, sdesc_sw64(ah + off), sdesc_sw64(bh + off), acc0);
-        umma_bf16(tmem, sdesc_sw64(ah + off), sdesc_sw64(bl + off), 1u);
-        umma_bf16(tmem, sdesc_sw64(al + off), sdesc_sw64(bh + off), 1u);
+        for (int kk = 0; kk < TK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 BF16 along K
+          // each chunk restarts its accumulator
+          const uint32_t acc0 = (kb > c * CHUNK_KB || kk > 0) ? 1u : 0u;
+          umma_bf16(acc_tm, sdesc_sw64(ah + off), sdesc_sw64(bh + off), acc0);
+          umma_bf16(acc_tm, sdesc_sw64(ah + off), sdesc_sw64(bl + off), 1u);
+          umma_bf16(acc_tm, sdesc_sw64(al + off), sdesc_sw64(bh + off), 1u);
+        }
+        umma_commit(smem_u32(&bars[STAGES + s]));  // stage free once these MMAs finish
       }
-      umma_commit(smem_u32(&bars[STAGES + s]));  // stage free once these MMAs finish
+      umma_commit(smem_u32(&bars[2 * STAGES + b]));  // chunk c ready (or aborted)
     }
-    umma_commit(smem_u32(&bars[2 * STAGES]));    // accumulator ready (or aborted)
+    if (!ok) {
+      s_abort = 1;
+      umma_commit(smem_u32(&bars[2 * STAGES]));
+      umma_commit(smem_u32(&bars[2 * STAGES + 1]));
+    }
   } else if (warp >= 2) {
     // ------------------------------------------------------- epilogue
-    const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0u, P.err, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;                  // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;           // complex columns [h*64, h*64 + 64) of the tile
     const int64_t row = m0 + q * 32 + lane;
-    // warp-uniform decision: tcgen05.ld is a whole-warp instruction
-    const bool go = __all_sync(0xffffffffu, ok && !*(volatile int*)&s_abort);
-    if (go) {
-      for (int jc = 0; jc < 4; ++jc) {
-        float re[32], im[32];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16);
-        tmem_ld32(ta + jc * 32, re);
-        tmem_ld32(ta + 128 + jc * 32, im);
-        if (row >= P.N) continue;
-#pragma unroll 4
-        for (int jj = 0; jj < 32; ++jj) {
-          const int64_t col = tile * 128 + jc * 32 + jj;
-          if (col < P.j0 || col >= P.ncols) continue;
-          const float2 yc = P.Ycur[row + col * P.N];
-          float2* yp = P.Yprev + row + col * P.N;
-          float vr = P.alpha * fmaf(-P.gamma, yc.x, re[jj]);
-          float vi = P.alpha * fmaf(-P.gamma, yc.y, im[jj]);
-          if (P.beta != 0.0f) {
-            const float2 y0 = *yp;
-            vr = fmaf(P.beta, y0.x, vr);
-            vi = fmaf(P.beta, y0.y, vi);
-          }
-          *yp = make_float2(vr, vi);
-          if (P.write_next) {
-            __nv_bfloat16 rh, rl, ih, il, nh, nl;
-            split2f(vr, rh, rl);
-            split2f(vi, ih, il);
-            split2f(-vi, nh, nl);
-            const int64_t br = brow_re(col), bi = br + 128, ld = 2 * P.Np;
-            P.Bn_hi[br * ld + row] = rh;
-            P.Bn_lo[br * ld + row] = rl;
-            P.Bn_hi[br * ld + P.Np + row] = nh;
-            P.Bn_lo[br * ld + P.Np + row] = nl;
-            P.Bn_hi[bi * ld + row] = ih;
-            P.Bn_lo[bi * ld + row] = il;
-            P.Bn_hi[bi * ld + P.Np + row] = rh;
-            P.Bn_lo[bi * ld + P.Np + row] = rl;
-          }
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    float sre[64], sim[64];                  // chunk sums, round-to-nearest FP32 adds
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      sre[j] = 0.f;
+      sim[j] = 0.f;
+    }
+    bool go = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES + b]), (uint32_t)(c >> 1) & 1u, P.err, 4);
+      // warp-uniform decision: tcgen05.ld is a whole-warp instruction
+      go = __all_sync(0xffffffffu, ok && !*(volatile int*)&s_abort);
+      if (!go) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ta = tl + (uint32_t)(b * TN + h * 64);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float v[32];
+        tmem_ld32(ta + half * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sre[half * 32 + j] += v[j];
+        tmem_ld32(ta + 128 + half * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sim[half * 32 + j] += v[j];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * STAGES + 2 + b]));
+    }
+    if (go && row < P.N) {
+#pragma unroll
+      for (int jj = 0; jj < 64; ++jj) {  // fully unrolled: the sums stay in registers
+        const int64_t col = tile * 128 + h * 64 + jj;
+        if (col < P.j0 || col >= P.ncols) continue;
+        const float2 yc = P.Ycur[row + col * P.N];
+        float2* yp = P.Yprev + row + col * P.N;
+        float vr = P.alpha * fmaf(-P.gamma, yc.x, sre[jj]);
+        float vi = P.alpha * fmaf(-P.gamma, yc.y, sim[jj]);
+        if (P.beta != 0.0f) {
+          const float2 y0 = *yp;
+          vr = fmaf(P.beta, y0.x, vr);
+          vi = fmaf(P.beta, y0.y, vi);
+        }
+        *yp = make_float2(vr, vi);
+        if (P.write_next) {
+          __nv_bfloat16 rh, rl, ih, il, nh, nl;
+          split2f(vr, rh, rl);
+          split2f(vi, ih, il);
+          split2f(-vi, nh, nl);
+          const int64_t br = brow_re(col), bi = br + 128, ld = 2 * P.Np;
+          P.Bn_hi[br * ld + row] = rh;
+          P.Bn_lo[br * ld + row] = rl;
+          P.Bn_hi[br * ld + P.Np + row] = nh;
+          P.Bn_lo[br * ld + P.Np + row] = nl;
+          P.Bn_hi[bi * ld + row] = ih;
+          P.Bn_lo[bi * ld + row] = il;
+          P.Bn_hi[bi * ld + P.Np + row] = rh;
+          P.Bn_lo[bi * ld + P.Np + row] = rl;
         }
       }
     }

@@ -17,9 +17,10 @@ with random signs to about sqrt(K) 2^-48 of max|a| max|y| per entry (six
 digits, levels 2-5 exact, 6-7 in FP32 per 256-long chunk). The bound per
 filter column is degs * 2^-42 * sqrt(K / 1400) of the column's largest entry,
 the N <= 700 bound of the small-size tests scaled by the sqrt(K) growth of the
-truncation error. Split-BF16 x3: degs * 2^-16 of the column's largest entry
-(measured worst 1.75e-4 at degree 36 at N <= 700, i.e. 4.9e-6 per degree;
-2^-16 = 1.5e-5 per degree leaves a factor 3). Measured values are printed.
+truncation error. Split-BF16 x3: degs * 2^-16 of the column's largest entry, the
+split products' own error (a CPU emulation of them gives 1.1e-5 per degree on
+this geometric spectrum); the tensor cores' FP32 accumulation enters only per
+256-long K chunk, so the bound does not grow with N. Measured values are printed.
 """
 import numpy as np
 import pytest

@@ -1,13 +1,15 @@
 """Tensor-core (tcgen05, split-BF16 x3) filter against the FP64 oracle.
 
 The mixed filter computes every HEMM of Eq. 1 as hi*hi + hi*lo + lo*hi BF16
-products with FP32 accumulation. Splitting x = hi + lo leaves |x - hi - lo| <=
-2^-17 |x| and the dropped lo*lo term is <= 2^-16 |a||y|, so one step carries a
-relative error of at most about 2^-15 of the operands' magnitudes; the FP64
-recurrence adds these step errors, which the normalised filter does not amplify
-in the columns' dominant directions. Bound used: per column j,
-max |Y_mixed - Y_oracle| <= degs[j] * 2^-15 * max |Y_oracle| (measured values
-are printed; they sit 5-10x below the bound).
+products, accumulated in FP32 tensor memory over K chunks of 256 and across
+chunks in FP32 registers. Splitting x = hi + lo leaves |x - hi - lo| <= 2^-17 |x|
+and the dropped lo*lo term is <= 2^-16 |a||y|, so one step carries a relative
+error of about 2^-16 of the operands' magnitudes; the recurrence adds these step
+errors, which the normalised filter does not amplify in the columns' dominant
+directions. A CPU emulation of the split products (FP64 accumulation) gives
+1.1e-5 per degree on a geometric spectrum and 3e-6 on a uniform one. Bound used:
+per column j, max |Y_mixed - Y_oracle| <= degs[j] * 2^-16 * max |Y_oracle|
+(measured values are printed).
 """
 import numpy as np
 import pytest
@@ -45,7 +47,7 @@ def test_mixed_filter_against_oracle(lib, N, ncols, dmax):
     rel = np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)
     print(f"N={N} ncols={ncols}: max rel err {rel.max():.3e} median {np.median(rel):.3e}")
     assert np.all(np.isfinite(got))
-    assert np.all(rel <= degs * 2.0 ** -15)
+    assert np.all(rel <= degs * 2.0 ** -16)
 
 
 def test_mixed_solve_c1_reaches_fp64_accuracy(lib):
