@@ -228,14 +228,19 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 // Returns the POTRF info through *info_h (0 = success; X untouched otherwise).
 //
 // With the tensor-core FP64 products (fp64_tensor):
-//  * Gram matrix. A digit-sliced X^H X has an error of about sqrt(N) 2^-47 of
-//    the product of the two columns' largest entries (FP64: sqrt(N) 2^-53 of the
-//    column norms' product). For the localised columns of nearly converged Ritz
-//    vectors (one entry near 1, the rest small) that is 1e-12 - 1e-11 of the
-//    column norms, and the orthogonality a pass delivers is the Gram error
-//    times kappa(X)^2. So only passes that are not the last of their variant
-//    (the next pass removes their error) use the tensor cores; every variant's
-//    last pass keeps the FP64 CUDA-core Gram.
+//  * Gram matrix. A digit-sliced X^H X carries an error of about
+//    sqrt(2N) 2^-48 2^(e_i + e_j), where 2^e_i (between 2 and 4 times the
+//    largest entry of column i) is the column's digit scale; FP64 gives about
+//    sqrt(N) 2^-53 of the column norms' product. The orthogonality a pass
+//    delivers is the Gram error times kappa(X)^2. Passes that are not the last
+//    of their variant (the next pass removes their error) use the tensor cores.
+//    The last pass of CholeskyQR2 / shifted CholeskyQR2 (input orthonormal to
+//    about the previous pass's kappa^2 u) uses them when that bound, with the
+//    largest column scale, stays below 1e-14: true for flat columns (a
+//    filtered block of mixed eigenvectors: 2^e ~ 10 / sqrt(N)), false for
+//    localised ones (nearly converged Ritz vectors with an entry near 1: the
+//    bound is 1e-11), which get the FP64 Gram. CholeskyQR1's single pass
+//    (kappa up to 20) always keeps the FP64 Gram.
 //  * X U^-1. When max |U - I| <= 1e-4 (the input is orthonormal to about 1e-4),
 //    X U^-1 = X + X D with D = U^-1 - I, |D| <= ~1e-4: the digit-sliced product
 //    X D carries an error of about sqrt(2n) 2^-44 max|X_i.| max|D_.j|, below
@@ -247,10 +252,12 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 //    largest and lose the span of the small columns.
 constexpr double kNearIdentity = 1e-4;
 
+constexpr double kGramTol = 1e-14;
+
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
-                bool last, int* info_h) {
+                bool last, bool single, int* info_h) {
   const bool tensor = c->p.fp64_tensor != 0;
-  const bool tc = tensor && !last;
+  bool tc = tensor && !single;
   double* dev_h = c->host + 2 * c->ne + 10;
   {
     if (tc) {
@@ -260,7 +267,17 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
       ep.ldy = c->ne;
       CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow));
       CK(hermitian_part(c->stream, n, c->G, c->ne));
-    } else {
+      if (last) {  // keep it only if its error bound allows (see above)
+        int* emax_h = reinterpret_cast<int*>(c->host + 2 * c->ne + 11);
+        CK(ozaki_left_exp_max(c->stream, n, c->ow, c->info + 1));
+        CK(cudaMemcpyAsync(emax_h, c->info + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        RC(ozaki_check(c->stream, c->ow));
+        const double bound = std::sqrt(2.0 * (double)c->N) * std::ldexp(1.0, 2 * *emax_h - 48);
+        tc = bound <= kGramTol;
+      }
+    }
+    if (!tc) {
       CK(zgram(c->stream, c->N, n, n, X, ldx, X, ldx, c->G, c->ne, true, c->gram_ws,
                c->gram_ws_elems));
     }
@@ -305,7 +322,7 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
     const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
     bool ok = true;
     for (int k = 0; k < passes && ok; ++k) {
-      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, info_h));
+      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, passes == 1, info_h));
       ok = (*info_h == 0);
     }
     if (ok) {
@@ -318,9 +335,9 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
   }
   // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2, then CholeskyQR2
   const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
-  RC(cholqr_pass(c, X, ldx, n, factor, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, info_h));
+  RC(cholqr_pass(c, X, ldx, n, factor, false, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, false, false, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, false, info_h));
   if (*info_h == 0) {
     if (variant) *variant = CHASE_QR_SHIFTED;
     return CHASE_OK;

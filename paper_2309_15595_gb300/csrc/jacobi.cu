@@ -545,8 +545,9 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   const int m = (int)(n + (n & 1));
   const int npairs = m / 2;
   const size_t smem = (size_t)2 * n * sizeof(C) + (size_t)8 * npairs * sizeof(T);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // the opt-in limit covers dynamic + static shared memory (the kernel's static
+  // reduction arrays add 4 KB), so it is set for every size, not only above 48 KB
+  if (cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return CHASE_CUDA_FAIL();
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;

@@ -758,6 +758,28 @@ cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const doubl
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void exp_max_kernel(int64_t n, const int* __restrict__ e, int* __restrict__ out) {
+  __shared__ int red[256];
+  int m = -100000;
+  for (int64_t i = threadIdx.x; i < n; i += 256) m = max(m, e[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+}  // namespace
+
+cudaError_t ozaki_left_exp_max(cudaStream_t s, int64_t M, OzakiWork& w, int* out) {
+  if (M <= 0) return cudaSuccess;
+  exp_max_kernel<<<1, 256, 0, s>>>(M, w.el, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 int ozaki_check(cudaStream_t s, OzakiWork& w) {
   int herr = 0;
   if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -39,6 +39,9 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
 cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const double2* X,
                                int64_t ldx, bool conj_trans, int64_t ncols, const double2* B,
                                int64_t ldb, const Epilogue& ep, OzakiWork& w);
+// *out (device) = the largest row exponent e of the last general product's left
+// operand (rows scaled by 2^-e to |x| < 1/2): bounds its digit-sliced error.
+cudaError_t ozaki_left_exp_max(cudaStream_t s, int64_t M, OzakiWork& w, int* out);
 // Reads and clears the device error flag; returns a chase_status.
 int ozaki_check(cudaStream_t s, OzakiWork& w);
 
