@@ -236,11 +236,12 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 //    of their variant (the next pass removes their error) use the tensor cores.
 //    The last pass of CholeskyQR2 / shifted CholeskyQR2 (input orthonormal to
 //    about the previous pass's kappa^2 u) uses them when that bound, with the
-//    largest column scale, stays below 1e-14: true for flat columns (a
-//    filtered block of mixed eigenvectors: 2^e ~ 10 / sqrt(N)), false for
-//    localised ones (nearly converged Ritz vectors with an entry near 1: the
-//    bound is 1e-11), which get the FP64 Gram. CholeskyQR1's single pass
-//    (kappa up to 20) always keeps the FP64 Gram.
+//    largest column scale, stays below 1e-13 (the orthogonality target is
+//    1e-12): true for flat columns (a filtered block that mixes many
+//    eigenvectors: 2^e ~ 5 - 10 / sqrt(N), bound ~1e-14), false for localised
+//    ones (nearly converged Ritz vectors with an entry near 1: bound ~1e-11),
+//    which get the FP64 Gram. CholeskyQR1's single pass (kappa up to 20) always
+//    keeps the FP64 Gram.
 //  * X U^-1. When max |U - I| <= 1e-4 (the input is orthonormal to about 1e-4),
 //    X U^-1 = X + X D with D = U^-1 - I, |D| <= ~1e-4: the digit-sliced product
 //    X D carries an error of about sqrt(2n) 2^-44 max|X_i.| max|D_.j|, below
@@ -252,7 +253,7 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 //    largest and lose the span of the small columns.
 constexpr double kNearIdentity = 1e-4;
 
-constexpr double kGramTol = 1e-14;
+constexpr double kGramTol = 1e-13;
 
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
                 bool last, bool single, int* info_h) {
