@@ -596,12 +596,13 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
     A(ozaki_alloc(c->ow, N, ne));
     if (ok) A(dalloc(&c->oz_partial, (size_t)cdiv(N, 32) * ne));
   }
-  if (ok) A(cudaMallocHost(reinterpret_cast<void**>(&c->host), (2 * ne + 16) * sizeof(double)));
+  if (ok) A(cudaMallocHost(reinterpret_cast<void**>(&c->host), (2 * ne + 16 + 512) * sizeof(double)));
   if (ok) A(cudaEventCreate(&c->ev0));
   if (ok) A(cudaEventCreate(&c->ev1));
   if (ok) A(cudaMemsetAsync(c->lw.status, 0, sizeof(int), c->stream));
   if (ok) {
     c->jw.host_red = c->host + 2 * ne + 12;
+    c->jw.host_part = c->host + 2 * ne + 16;
     c->jw.gram_ws = c->gram_ws;
     c->jw.gram_ws_elems = c->gram_ws_elems;
     c->jw.dinv = c->dinv;

@@ -161,6 +161,7 @@ struct JacobiWork {
   double* params;    // 4 per pair
   double* red;       // reduction scratch
   double* host_red;  // pinned host scalars
+  double* host_part = nullptr;  // pinned host: 512 doubles of partial sums
   int64_t nmax;
   int max_sweeps = 0;  // > 0: cap on every stage (sweeps, refinement steps)
   int* pairs = nullptr;   // index pairs the refinement could not separate (2 ints each)

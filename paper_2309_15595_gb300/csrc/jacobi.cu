@@ -602,6 +602,307 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   return CHASE_OK;
 }
 
+// ------------------------------------------------------ blocked FP32 Jacobi
+// The FP32 stage as a block Jacobi method: the columns are cut into blocks of
+// BJ_B, the blocks are paired in round-robin order (as the scalar method pairs
+// columns), and per round every block pair's 2 BJ_B x 2 BJ_B principal
+// submatrix S is diagonalised by one cyclic Jacobi sweep in shared memory,
+// which accumulates its rotations into R (S <- R^H S R). The pair's columns of
+// G and Z are then multiplied by R and its rows of G by R^H, as small GEMMs.
+// Pairs of one round touch disjoint columns (and rows), so they run in
+// parallel; a sweep visits every block pair once. Compared with one scalar
+// rotation per column pair and round, the matrix streams through memory
+// BJ_B times less often.
+constexpr int BJ_B = 32;          // block width
+constexpr int BJ_M = 2 * BJ_B;    // order of a block pair
+constexpr int BJ_T = 256;
+constexpr int BJ_ROWS = 64;       // rows (or columns) of G per CTA in the update kernels
+constexpr int BJ_UPD_SMEM = (BJ_M * (BJ_M + 1) + BJ_ROWS * (BJ_M + 1)) * (int)sizeof(float2);
+
+__device__ __forceinline__ void bj_pair(int64_t n, int nb, int nbp, int round, int k, int64_t& i0,
+                                        int& ni, int64_t& j0, int& nj) {
+  auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (nbp - 1); };
+  int p = pos(k), q = pos(nbp - 1 - k);
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+  i0 = (int64_t)p * BJ_B;
+  j0 = (int64_t)q * BJ_B;
+  ni = p < nb ? (int)min((int64_t)BJ_B, n - i0) : 0;
+  nj = q < nb ? (int)min((int64_t)BJ_B, n - j0) : 0;
+}
+// global index of local index a of a block pair (first block, then second)
+__device__ __forceinline__ int64_t bj_gidx(int a, int64_t i0, int ni, int64_t j0) {
+  return a < ni ? i0 + a : j0 + (a - ni);
+}
+
+constexpr int BJ_INNER_SMEM = 2 * BJ_M * (BJ_M + 1) * (int)sizeof(float2);
+
+__global__ void __launch_bounds__(BJ_T)
+    bj_inner_kernel(int64_t n, int nb, int nbp, int round, const float2* __restrict__ G,
+                    float2* __restrict__ Rbuf) {
+  extern __shared__ float2 bj_smem[];
+  float2 (*S)[BJ_M + 1] = reinterpret_cast<float2 (*)[BJ_M + 1]>(bj_smem);
+  float2 (*R)[BJ_M + 1] = reinterpret_cast<float2 (*)[BJ_M + 1]>(bj_smem + BJ_M * (BJ_M + 1));
+  __shared__ RotT<float> rots[BJ_M / 2];
+  const int k = blockIdx.x, t = threadIdx.x;
+  int64_t i0, j0;
+  int ni, nj;
+  bj_pair(n, nb, nbp, round, k, i0, ni, j0, nj);
+  const int m = ni + nj;
+  for (int e = t; e < m * m; e += BJ_T) {
+    const int a = e % m, c = e / m;
+    S[a][c] = G[bj_gidx(a, i0, ni, j0) + bj_gidx(c, i0, ni, j0) * n];
+    R[a][c] = make_float2(a == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int mp = m + (m & 1);
+  for (int rd = 0; rd < mp - 1; ++rd) {
+    if (t < mp / 2) {
+      int p, q;
+      rr_pair(mp, rd, t, p, q);
+      rots[t] = q < m ? make_rot_t<float>(S[p][p].x, S[q][q].x, S[p][q])
+                      : make_rot_t<float>(0.f, 0.f, make_float2(0.f, 0.f));
+    }
+    __syncthreads();
+    for (int e = t; e < (mp / 2) * m; e += BJ_T) {  // column rotations of S and R
+      const int kk = e / m, i = e % m;
+      int p, q;
+      rr_pair(mp, rd, kk, p, q);
+      if (q >= m || rots[kk].s == 0.f) continue;
+      rot_cols_t(S[i][p], S[i][q], rots[kk]);
+      rot_cols_t(R[i][p], R[i][q], rots[kk]);
+    }
+    __syncthreads();
+    for (int e = t; e < (mp / 2) * m; e += BJ_T) {  // row rotations of S
+      const int kk = e / m, j = e % m;
+      int p, q;
+      rr_pair(mp, rd, kk, p, q);
+      if (q >= m || rots[kk].s == 0.f) continue;
+      rot_rows_t(S[p][j], S[q][j], rots[kk]);
+    }
+    __syncthreads();
+    if (t < mp / 2) {  // the rotated 2 x 2 block exactly
+      int p, q;
+      rr_pair(mp, rd, t, p, q);
+      if (q < m && rots[t].s != 0.f) {
+        S[p][p] = make_float2(rots[t].app, 0.f);
+        S[q][q] = make_float2(rots[t].aqq, 0.f);
+        S[p][q] = make_float2(0.f, 0.f);
+        S[q][p] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+  }
+  float2* Rk = Rbuf + (int64_t)k * BJ_M * BJ_M;
+  for (int e = t; e < m * m; e += BJ_T) Rk[(e % m) + (e / m) * BJ_M] = R[e % m][e / m];
+}
+
+// Columns of the pair: M(r0:r0+64, idx) <- M(r0:r0+64, idx) R for M = G and Z.
+__global__ void __launch_bounds__(BJ_T)
+    bj_cols_kernel(int64_t n, int nb, int nbp, int round, float2* __restrict__ G,
+                   float2* __restrict__ Z, const float2* __restrict__ Rbuf) {
+  extern __shared__ float2 bj_smem[];
+  float2* R = bj_smem;                      // [BJ_M][BJ_M + 1]
+  float2* T = bj_smem + BJ_M * (BJ_M + 1);  // [BJ_ROWS][BJ_M + 1]
+  const int k = blockIdx.y, t = threadIdx.x;
+  int64_t i0, j0;
+  int ni, nj;
+  bj_pair(n, nb, nbp, round, k, i0, ni, j0, nj);
+  const int m = ni + nj;
+  if (m == 0) return;
+  const float2* Rk = Rbuf + (int64_t)k * BJ_M * BJ_M;
+  for (int e = t; e < m * m; e += BJ_T) R[(e % m) * (BJ_M + 1) + e / m] = Rk[(e % m) + (e / m) * BJ_M];
+  const int64_t r0 = (int64_t)blockIdx.x * BJ_ROWS;
+  const int tx = t & 15, ty = t >> 4;  // columns tx + 16 c, rows ty + 16 r
+  for (int mat = 0; mat < 2; ++mat) {
+    float2* M = mat == 0 ? G : Z;
+    __syncthreads();
+    for (int e = t; e < BJ_ROWS * m; e += BJ_T) {
+      const int i = e % BJ_ROWS, a = e / BJ_ROWS;
+      const int64_t row = r0 + i;
+      T[i * (BJ_M + 1) + a] =
+          row < n ? M[row + bj_gidx(a, i0, ni, j0) * n] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 o[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) o[r][c] = make_float2(0.f, 0.f);
+    for (int a = 0; a < m; ++a) {
+      float2 x[4], y[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[r] = T[(ty + 16 * r) * (BJ_M + 1) + a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[c] = R[a * (BJ_M + 1) + tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          o[r][c].x = fmaf(x[r].x, y[c].x, fmaf(-x[r].y, y[c].y, o[r][c].x));
+          o[r][c].y = fmaf(x[r].x, y[c].y, fmaf(x[r].y, y[c].x, o[r][c].y));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t row = r0 + ty + 16 * r;
+      if (row >= n) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int cc = tx + 16 * c;
+        if (cc < m) M[row + bj_gidx(cc, i0, ni, j0) * n] = o[r][c];
+      }
+    }
+  }
+}
+
+// Rows of the pair: G(idx, c0:c0+64) <- R^H G(idx, c0:c0+64).
+__global__ void __launch_bounds__(BJ_T)
+    bj_rows_kernel(int64_t n, int nb, int nbp, int round, float2* __restrict__ G,
+                   const float2* __restrict__ Rbuf) {
+  extern __shared__ float2 bj_smem[];
+  float2* R = bj_smem;                      // [BJ_M][BJ_M + 1]
+  float2* T = bj_smem + BJ_M * (BJ_M + 1);  // [BJ_M][BJ_ROWS + 1] (rows of the pair x columns)
+  const int k = blockIdx.y, t = threadIdx.x;
+  int64_t i0, j0;
+  int ni, nj;
+  bj_pair(n, nb, nbp, round, k, i0, ni, j0, nj);
+  const int m = ni + nj;
+  if (m == 0) return;
+  const float2* Rk = Rbuf + (int64_t)k * BJ_M * BJ_M;
+  for (int e = t; e < m * m; e += BJ_T) R[(e % m) * (BJ_M + 1) + e / m] = Rk[(e % m) + (e / m) * BJ_M];
+  const int64_t c0 = (int64_t)blockIdx.x * BJ_ROWS;
+  for (int e = t; e < m * BJ_ROWS; e += BJ_T) {
+    const int a = e % m, j = e / m;
+    const int64_t col = c0 + j;
+    T[a * (BJ_ROWS + 1) + j] = col < n ? G[bj_gidx(a, i0, ni, j0) + col * n] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int tx = t & 15, ty = t >> 4;  // columns tx + 16 c, pair rows ty + 16 r
+  float2 o[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[r][c] = make_float2(0.f, 0.f);
+  for (int b = 0; b < m; ++b) {
+    float2 x[4], y[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int a = ty + 16 * r;  // (R^H)(a, b) = conj(R(b, a))
+      const float2 rv = a < m ? R[b * (BJ_M + 1) + a] : make_float2(0.f, 0.f);
+      x[r] = make_float2(rv.x, -rv.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = T[b * (BJ_ROWS + 1) + tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        o[r][c].x = fmaf(x[r].x, y[c].x, fmaf(-x[r].y, y[c].y, o[r][c].x));
+        o[r][c].y = fmaf(x[r].x, y[c].y, fmaf(x[r].y, y[c].x, o[r][c].y));
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int a = ty + 16 * r;
+    if (a >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t col = c0 + tx + 16 * c;
+      if (col < n) G[bj_gidx(a, i0, ni, j0) + col * n] = o[r][c];
+    }
+  }
+}
+
+// Off-diagonal and total squared Frobenius norms of G (n x n, FP32): one
+// partial pair per block, summed on the host in a fixed order.
+__global__ void bj_norms_kernel(int64_t n, const float2* __restrict__ G, double* __restrict__ part) {
+  __shared__ double so[256], sf[256];
+  double o = 0.0, f = 0.0;
+  const int64_t tot = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < tot; e += (int64_t)gridDim.x * 256) {
+    const float2 g = G[e];
+    const double v = (double)g.x * g.x + (double)g.y * g.y;
+    f += v;
+    if (e % n != e / n) o += v;
+  }
+  so[threadIdx.x] = o;
+  sf[threadIdx.x] = f;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) {
+      so[threadIdx.x] += so[threadIdx.x + w];
+      sf[threadIdx.x] += sf[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = so[0];
+    part[2 * blockIdx.x + 1] = sf[0];
+  }
+}
+
+std::once_flag g_bj_attr[kMaxDevices];
+
+// Blocked FP32 Jacobi on G (n x n, destroyed) with eigenvectors into Z (starts
+// as I): sweeps until off(G) <= tol_conv ||G||_F, or <= tol_stag ||G||_F with
+// less than a 4x decrease in the last sweep, or max_sweeps. part: 512 doubles
+// of device scratch, host_part: 512 doubles of host memory.
+int run_block_jacobi32(cudaStream_t s, int64_t n, float2* G, float2* Z, float2* Rbuf,
+                       double* part, double* host_part, int max_sweeps, double tol_conv,
+                       double tol_stag, int* sweeps, bool* conv) {
+  once_per_device(g_bj_attr, []() {
+    cudaFuncSetAttribute(bj_inner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         BJ_INNER_SMEM);
+    cudaFuncSetAttribute(bj_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_UPD_SMEM);
+    cudaFuncSetAttribute(bj_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BJ_UPD_SMEM);
+  });
+  const int nb = (int)cdiv(n, BJ_B);
+  const int nbp = nb + (nb & 1);
+  const int npair = nbp / 2;
+  const unsigned gt = (unsigned)cdiv(n, BJ_ROWS);
+  constexpr int kNormBlocks = 256;
+  double off_prev = 1e300;
+  *conv = false;
+  int sw = 0;
+  for (; sw <= max_sweeps; ++sw) {
+    bj_norms_kernel<<<kNormBlocks, 256, 0, s>>>(n, G, part);
+    count_launch();
+    if (cudaMemcpyAsync(host_part, part, 2 * kNormBlocks * sizeof(double), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CHASE_CUDA_FAIL();
+    double o = 0.0, f = 0.0;
+    for (int b = 0; b < kNormBlocks; ++b) {
+      o += host_part[2 * b];
+      f += host_part[2 * b + 1];
+    }
+    const double off = std::sqrt(o), fro = std::sqrt(f);
+    if (off == 0.0 || off <= tol_conv * fro || (off <= tol_stag * fro && off > 0.25 * off_prev)) {
+      *conv = true;
+      break;
+    }
+    off_prev = off;
+    if (sw == max_sweeps) break;
+    for (int rd = 0; rd < nbp - 1; ++rd) {
+      bj_inner_kernel<<<npair, BJ_T, BJ_INNER_SMEM, s>>>(n, nb, nbp, rd, G, Rbuf);
+      bj_cols_kernel<<<dim3(gt, (unsigned)npair, 1), BJ_T, BJ_UPD_SMEM, s>>>(n, nb, nbp, rd, G, Z,
+                                                                          Rbuf);
+      bj_rows_kernel<<<dim3(gt, (unsigned)npair, 1), BJ_T, BJ_UPD_SMEM, s>>>(n, nb, nbp, rd, G,
+                                                                          Rbuf);
+      count_launch();
+      count_launch();
+      count_launch();
+    }
+    if (cudaGetLastError() != cudaSuccess) return CHASE_CUDA_FAIL();
+  }
+  *sweeps = sw;
+  return CHASE_OK;
+}
+
 __global__ void rank_kernel(int64_t n, const double2* Gw, double* w, int* rank) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1003,12 +1304,13 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   const dim3 g2((unsigned)cdiv(n, 128), (unsigned)n, 1);
   init32_kernel<<<g2, 128, 0, s>>>(n, G, ldg, wk.G32a, wk.Z32); count_launch();
   int sw32 = 0;
-  bool conv32 = false, in_g1 = false;
+  bool conv32 = false;
   // stage caps: 30 FP32 sweeps, 8 refinement steps, kMaxSweeps FP64 sweeps, each
   // lowered to the caller's cap when one is set
   auto cap = [&](int def) { return wk.max_sweeps > 0 ? std::min(def, wk.max_sweeps) : def; };
-  RC_(run_coop<float>(s, n, wk.G32a, wk.G32b, wk.Z32, reinterpret_cast<float*>(wk.params), wk.red,
-                      cap(30), 4e-6, 1e-4, &sw32, &conv32, &in_g1));
+  // blocked FP32 Jacobi: G32a is G (in place), G32b the block rotations
+  RC_(run_block_jacobi32(s, n, wk.G32a, wk.Z32, wk.G32b, wk.red, wk.host_part, cap(30), 4e-6, 1e-4,
+                         &sw32, &conv32));
   // --- FP64: refine the FP32 eigenvectors (Ogita-Aishima steps, FP64 GEMMs)
   promote_kernel<<<g2, 128, 0, s>>>(n, wk.Z32, wk.Zw); count_launch();
   const unsigned gb = (unsigned)cdiv(n, 256);
