@@ -86,7 +86,7 @@ void free_ctx(chase_ctx* c) {
   void* bufs[] = {c->V2, c->W, c->G, c->Yeig, c->gram_ws, c->dinv, c->info, c->resid_partial,
                   c->dscal, c->perm_d, c->jw.Gw, c->jw.Gw2, c->jw.Zw, c->jw.Zw2, c->jw.T,
                   c->jw.G32a, c->jw.G32b, c->jw.Z32, c->jw.params, c->jw.red,
-                  c->jw.pairs, c->jw.npairs, c->jw.cl_idx, c->jw.cl_off,
+                  c->jw.pairs, c->jw.npairs, c->jw.cl_idx, c->jw.cl_off, c->jw.Rb,
                   c->lw.Q, c->lw.ws, c->lw.red, c->lw.ab, c->lw.T, c->lw.theta, c->lw.Z,
                   c->lw.out4, c->lw.status};
   for (void* b : bufs)
@@ -575,6 +575,8 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   A(dalloc(&c->jw.Z32, (size_t)ne * ne));
   A(dalloc(&c->jw.params, jacobi_params_elems(ne)));
   A(dalloc(&c->jw.red, std::max<size_t>(1024, jacobi_red_elems())));
+  c->jw.rb_elems = jacobi_rot_elems(ne);
+  A(dalloc(&c->jw.Rb, c->jw.rb_elems));
   A(dalloc(&c->jw.pairs, (size_t)2 * kMaxClusterPairs));
   A(dalloc(&c->jw.npairs, 1));
   A(dalloc(&c->jw.cl_idx, (size_t)ne));

@@ -154,6 +154,8 @@ struct JacobiWork {
   float2* G32a;      // FP32 stage: two working copies and the eigenvectors
   float2* G32b;
   float2* Z32;
+  float2* Rb = nullptr;  // blocked FP32 Jacobi: one 64 x 64 rotation per block pair
+  size_t rb_elems = 0;
   double2* gram_ws;  // borrowed from the context (free while Jacobi runs)
   size_t gram_ws_elems;
   double2* dinv;     // borrowed: POTRF diagonal-block inverses and info
@@ -176,6 +178,8 @@ struct JacobiWork {
   void* gemm_ctx = nullptr;
 };
 size_t jacobi_params_elems(int64_t n);
+// float2 elements of JacobiWork::Rb for matrices up to order n
+size_t jacobi_rot_elems(int64_t n);
 constexpr int kMaxClusterPairs = 1 << 16;  // capacity of JacobiWork::pairs
 size_t jacobi_red_elems();  // doubles of JacobiWork::red
 // cluster_out (3 ints, may be null): [0] 1 if the pairs the FP64 refinement

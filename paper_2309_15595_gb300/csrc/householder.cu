@@ -20,6 +20,7 @@
 // sum of the partials), so results are reproducible run to run.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 #include "householder.cuh"
 
@@ -352,6 +353,7 @@ int householder_qr(cudaStream_t s, int64_t m, int64_t n, double2* X, int64_t ldx
   HK(cudaMemcpyAsync(&bad, w.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   HK(cudaStreamSynchronize(s));
 #undef HK
+  if (bad) fprintf(stderr, "[chase] Householder QR: the block holds non-finite values\n");
   return bad ? CHASE_ERR_QR_BREAKDOWN : CHASE_OK;
 }
 

@@ -545,11 +545,18 @@ int run_coop(cudaStream_t s, int64_t n, typename Cx<T>::C* G0, typename Cx<T>::C
   const int m = (int)(n + (n & 1));
   const int npairs = m / 2;
   const size_t smem = (size_t)2 * n * sizeof(C) + (size_t)8 * npairs * sizeof(T);
-  // the opt-in limit covers dynamic + static shared memory (the kernel's static
-  // reduction arrays add 4 KB), so it is set for every size, not only above 48 KB
-  if (cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return CHASE_CUDA_FAIL();
+  // The opt-in limit covers dynamic + static shared memory (the kernel's static
+  // reduction arrays add 4 KB, so sizes just under 48 KB need it too). It is a
+  // process-wide property of the function that concurrent solves on other host
+  // threads share, so it is set once per device to the largest size any
+  // context can ask for (n <= 3500), never lowered.
+  static std::once_flag attr_once[kMaxDevices];
+  once_per_device(attr_once, []() {
+    constexpr int64_t nmax = 3500;
+    const size_t most = (size_t)2 * nmax * sizeof(C) + (size_t)8 * (nmax / 2) * sizeof(T);
+    cudaFuncSetAttribute(jacobi_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)most);
+  });
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1139,6 +1146,11 @@ cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, co
 }
 }  // namespace
 
+size_t jacobi_rot_elems(int64_t n) {
+  const int64_t nb = cdiv(n, BJ_B);
+  return (size_t)((nb + 1) / 2) * BJ_M * BJ_M;
+}
+
 size_t jacobi_params_elems(int64_t n) { return (size_t)8 * (n / 2 + 2) + 8 + n; }
 
 cudaError_t jacobi_small_batched(cudaStream_t s, int n, int batch, const double2* G, double* w,
@@ -1308,8 +1320,9 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   // stage caps: 30 FP32 sweeps, 8 refinement steps, kMaxSweeps FP64 sweeps, each
   // lowered to the caller's cap when one is set
   auto cap = [&](int def) { return wk.max_sweeps > 0 ? std::min(def, wk.max_sweeps) : def; };
-  // blocked FP32 Jacobi: G32a is G (in place), G32b the block rotations
-  RC_(run_block_jacobi32(s, n, wk.G32a, wk.Z32, wk.G32b, wk.red, wk.host_part, cap(30), 4e-6, 1e-4,
+  // blocked FP32 Jacobi: G32a is G (in place), Rb the block rotations
+  if (jacobi_rot_elems(n) > wk.rb_elems) return CHASE_ERR_INVALID_ARG;
+  RC_(run_block_jacobi32(s, n, wk.G32a, wk.Z32, wk.Rb, wk.red, wk.host_part, cap(30), 4e-6, 1e-4,
                          &sw32, &conv32));
   // --- FP64: refine the FP32 eigenvectors (Ogita-Aishima steps, FP64 GEMMs)
   promote_kernel<<<g2, 128, 0, s>>>(n, wk.Z32, wk.Zw); count_launch();

@@ -315,22 +315,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // 2^-48, 2^-56, at most 2^-24 of the leading level) go to FP32 registers
       // per chunk. (Accumulating them in TMEM over the whole K range instead
       // lost accuracy at K = 80000: a Ritz-value floor near 1e-10 ||A||.)
+      // loads issued two levels at a time, one wait per pair (the TMEM load
+      // latency is paid 6 times per chunk instead of 12)
 #pragma unroll
-      for (int L = 2; L <= OS + 1; ++L) {
+      for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
-          float v[HC];
-          tmem_ld16(tl + (uint32_t)((L - 2) * TN + part * CT + h * HC), v);
+        for (int g = 0; g < 3; ++g) {         // levels 2-3, 4-5, 6-7
+          float v[2][HC];
+#pragma unroll
+          for (int l = 0; l < 2; ++l)
+            tmem_ld16(tl + (uint32_t)((2 * g + l) * TN + part * CT + h * HC), v[l]);
           tmem_wait_ld();
-          if (L <= 5) {
-            const int sh = 8 * (5 - L);
 #pragma unroll
-            for (int j = 0; j < HC; ++j)
-              acc[part * HC + j] += (long long)__float2int_rn(v[j]) << sh;
-          } else {
-            const float w = L == 6 ? 1.0f : 0.00390625f;
+          for (int l = 0; l < 2; ++l) {
+            const int L = 2 + 2 * g + l;
+            if (L <= 5) {
+              const int sh = 8 * (5 - L);
 #pragma unroll
-            for (int j = 0; j < HC; ++j) acc67[part * HC + j] = fmaf(w, v[j], acc67[part * HC + j]);
+              for (int j = 0; j < HC; ++j)
+                acc[part * HC + j] += (long long)__float2int_rn(v[l][j]) << sh;
+            } else {
+              const float w = L == 6 ? 1.0f : 0.00390625f;
+#pragma unroll
+              for (int j = 0; j < HC; ++j)
+                acc67[part * HC + j] = fmaf(w, v[l][j], acc67[part * HC + j]);
+            }
           }
         }
       }
