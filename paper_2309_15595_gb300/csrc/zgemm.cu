@@ -6,6 +6,8 @@
 // 256 threads with 4 x 4 complex accumulators each, and double-buffered shared
 // memory; the epilogues fuse the Chebyshev three-term update (Eq. 1), plain
 // stores, and the per-column residual sums of squares (Alg. 2 residual lines).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace chase {
@@ -329,11 +331,22 @@ cudaError_t zgram(cudaStream_t s, int64_t K, int64_t m, int64_t n, const double2
   if (ws_elems < (size_t)m * n) return cudaErrorInvalidValue;  // no room for one partial
   const int64_t tm = cdiv(m, BM), tn = cdiv(n, BN);
   const int64_t tiles = hermitian ? tm * (tm + 1) / 2 : tm * tn;
-  int64_t splits = cdiv(3 * num_sms(), tiles);
-  splits = std::min<int64_t>(splits, kMaxSplits);
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, K / 512));
-  splits = std::min<int64_t>(splits, (int64_t)(ws_elems / ((size_t)m * n)));
-  if (splits < 1) splits = 1;
+  // split-K factor: the one (up to the workspace, 8, and K / 512) whose CTA
+  // count fills the last wave best (3 resident CTAs per SM); ties to fewer splits
+  const int64_t slots = 3 * (int64_t)num_sms();
+  const int64_t smax = std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)kMaxSplits, std::max<int64_t>(1, K / 512),
+                            (int64_t)(ws_elems / ((size_t)m * n))}));
+  int64_t splits = 1;
+  double best = -1.0;
+  for (int64_t sp = 1; sp <= smax; ++sp) {
+    const int64_t ctas = tiles * sp;
+    const double eff = (double)ctas / (double)(cdiv(ctas, slots) * slots);
+    if (eff > best + 1e-9) {
+      best = eff;
+      splits = sp;
+    }
+  }
   const int64_t kchunk = cdiv(cdiv(K, splits), BK) * BK;
   Epilogue ep{};
   ep.mode = EPI_STORE;
