@@ -20,7 +20,9 @@
  *     chase_rayleigh_ritz) synchronise that stream before returning; the others
  *     return after enqueueing.
  *   - The library allocates all of its workspace in chase_create and frees it in
- *     chase_destroy; no other call allocates device memory.
+ *     chase_destroy; apart from chase_solve_batch's small launch table and the
+ *     gradient calls' workspace (documented below), no other call allocates
+ *     device memory.
  *   - Every call returns a chase_status. On CHASE_ERR_INVALID_ARG nothing was
  *     enqueued. On CHASE_ERR_CUDA the context should be destroyed.
  *   - A context is not thread-safe; use one context per host thread.
@@ -161,8 +163,10 @@ CHASE_API int chase_lanczos(struct chase_ctx* ctx, const chase_c128* A, int64_t 
  * T_m((A-cI)/e) if scaled_filter = 0). degs is a HOST array of ncols EVEN
  * degrees >= 2, sorted ascending (Section 3.1 even-degree rule; Alg. 1 sort).
  * precision: CHASE_FP64 or CHASE_MIXED_BF16X3 (the latter needs a context
- * created with that precision). Requires e > 0 and mu_1 <= c - e, so that
- * the normalisation T_m((mu_1 - c)/e) never vanishes. */
+ * created with that precision; its first call for a given N and column count
+ * on a device times the tensor-core kernel's raster orders once and keeps the
+ * fastest, which never changes a result). Requires e > 0 and mu_1 <= c - e, so
+ * that the normalisation T_m((mu_1 - c)/e) never vanishes. */
 CHASE_API int chase_filter(struct chase_ctx* ctx, const chase_c128* A, int64_t lda,
                  chase_c128* V, int64_t ldv, int64_t ncols, const int32_t* degs,
                  double c, double e, double mu_1, int32_t precision);
@@ -222,17 +226,26 @@ CHASE_API int chase_residuals_noalloc(const chase_c128* A, int64_t lda, const ch
 
 /* Many independent solves at once: problem k is chase_solve(ctxs[k], A[k],
  * lda[k], V[k], ldv[k], Q0 ? Q0[k] : NULL, ldq ? ldq[k] : 0, ritz[k],
- * resid[k], stats ? &stats[k] : NULL), run from one of `threads` host threads
- * (<= 0: 8; never more than count) on its context's own stream, largest
- * N^2 (nev + nex) first, so that the kernels of different problems overlap on
- * the GPU. Each problem's results are exactly those of chase_solve on it
- * alone. Warm starts (a sequence of related matrices, Section 1) pass the
- * previous Ritz vectors as V. The contexts must be distinct and should be
- * bound to distinct streams (problems sharing a stream run one after the
- * other); each context's device is made current on its worker thread.
- * status[k] receives each return code; the call returns CHASE_OK if all are
- * CHASE_OK, else the first non-OK status in problem order. The paper solves
- * one problem at a time; this batching has no counterpart there. */
+ * resid[k], stats ? &stats[k] : NULL), and each problem's results are exactly
+ * those of chase_solve on it alone. The problems advance through Alg. 2 in
+ * lockstep, phase by phase. `threads` host threads (<= 0: 8) run every
+ * problem's Lanczos start, degree/sort/CondEst step and QR / Rayleigh-Ritz /
+ * residual / locking step on the problem's own context and stream (largest
+ * N^2 (nev + nex) first), so that small problems overlap on the GPU. The
+ * filter phase of all problems in the reduced-precision mode on one device
+ * runs as one CUDA graph of grouped tensor-core launches, one launch per
+ * degree step covering every such problem's tiles; problems in the FP64 mode
+ * filter with their own launches. The tensor-core filter's raster order is
+ * chosen per shape by timing on its first use (see chase_filter). Warm starts
+ * (a sequence of related matrices, Section 1) pass the previous Ritz vectors
+ * as V. The contexts must be distinct. This call creates one extra stream per
+ * device that holds grouped problems and a small table of launch parameters
+ * (device and pinned host memory, about 640 bytes per problem and degree
+ * step), and frees both before returning. In stats, the grouped filter's time
+ * and launches are charged to every problem of the group. status[k] receives
+ * each return code; the call returns CHASE_OK if all are CHASE_OK, else the
+ * first non-OK status in problem order. The paper solves one problem at a
+ * time; this batching has no counterpart there. */
 CHASE_API int chase_solve_batch(int64_t count, struct chase_ctx* const* ctxs,
                                 const chase_c128* const* A, const int64_t* lda,
                                 chase_c128* const* V, const int64_t* ldv,

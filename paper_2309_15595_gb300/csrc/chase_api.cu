@@ -472,6 +472,251 @@ int lanczos_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q0,
 
 }  // namespace
 
+// ============================================================ solve phases
+namespace chase {
+namespace {
+// adds the kernels launched on this thread while it lives to S.launches
+struct LaunchTally {
+  SolveState& S;
+  long long l0;
+  explicit LaunchTally(SolveState& s) : S(s), l0(launch_count()) {}
+  ~LaunchTally() { S.launches += launch_count() - l0; }
+};
+}  // namespace
+
+SolveState::~SolveState() {
+  if (t_start) cudaEventDestroy(t_start);
+  if (t_end) cudaEventDestroy(t_end);
+  if (c) c->oz_a_valid = false;
+}
+
+int solve_begin(SolveState& S, chase_ctx* c, const double2* A, int64_t lda, double2* C,
+                int64_t ldv, const double2* Q0, int64_t ldq, double* ritz, double* resid) {
+  if (!c || !A || !C || !ritz || !resid || lda < c->N || ldv < c->N)
+    return CHASE_ERR_INVALID_ARG;
+  if (Q0 && ldq < c->N) return CHASE_ERR_INVALID_ARG;
+  if (!Q0 && c->p.lanczos_vecs > c->ne) return CHASE_ERR_INVALID_ARG;
+  const chase_params& P = c->p;
+  const int64_t ne = c->ne;
+  S.c = c;
+  S.A = A;
+  S.lda = lda;
+  S.C = C;
+  S.ldv = ldv;
+  S.ritz = ritz;
+  S.resid = resid;
+  std::memset(&S.st, 0, sizeof(S.st));
+  CK(cudaEventCreate(&S.t_start));
+  CK(cudaEventCreate(&S.t_end));
+  CK(cudaEventRecord(S.t_start, c->stream));
+  S.launches = 0;
+  LaunchTally tally(S);
+  if (P.fp64_tensor) {  // digits of A once for every tensor-core FP64 product of this solve
+    c->oz_a_valid = false;
+    RC(prepare_a(c, A, lda));
+    c->oz_a_valid = true;
+  }
+  double b4[4];
+  {
+    PhaseTimer tm(c, &S.st.ms_lanczos);
+    RC(lanczos_impl(c, A, lda, Q0 ? Q0 : C, Q0 ? ldq : ldv, P.lanczos_vecs, b4));
+  }
+  S.b_sup = b4[0];
+  S.mu_1 = b4[1];
+  S.mu_ne = b4[2];
+  S.norm_est = b4[3];
+  S.st.b_sup = S.b_sup;
+  S.st.mu_1 = S.mu_1;
+  S.st.mu_ne = S.mu_ne;
+  S.st.norm_est = S.norm_est;
+  S.tol_abs = P.tol * S.norm_est;
+  S.degs.assign(ne, P.deg_init);
+  S.rz.assign(ne, 0.0);
+  S.rs.assign(ne, 0.0);
+  S.locked = 0;
+  S.iter = 1;
+  S.cc = (S.b_sup + S.mu_ne) / 2.0;
+  S.ee = (S.b_sup - S.mu_ne) / 2.0;
+  S.mixed = P.precision == CHASE_MIXED_BF16X3;
+  S.rmax_prev = 1e300;
+  S.st.switch_iter = S.mixed ? -1 : 0;
+  return CHASE_OK;
+}
+
+bool solve_active(const SolveState& S) {
+  return S.locked < S.c->p.nev && S.iter <= S.c->p.max_iter;
+}
+
+int solve_prepare(SolveState& S) {
+  LaunchTally tally(S);
+  chase_ctx* c = S.c;
+  const chase_params& P = c->p;
+  const int64_t N = c->N, ne = c->ne, locked = S.locked, nact = ne - locked;
+  double2* C = S.C;
+  const int64_t ldv = S.ldv;
+  std::vector<int32_t>& degs = S.degs;
+  std::vector<double>& rz = S.rz;
+  std::vector<double>& rs = S.rs;
+  if (S.iter != 1) {
+    S.mu_1 = *std::min_element(rz.begin(), rz.end());
+    S.mu_ne = *std::max_element(rz.begin(), rz.end());
+    S.cc = (S.b_sup + S.mu_ne) / 2.0;
+    S.ee = (S.b_sup - S.mu_ne) / 2.0;
+    if (P.deg_opt) {
+      chase_degree_opt(rs.data() + locked, rz.data() + locked, nact, S.cc, S.ee, S.tol_abs,
+                       P.deg_max, P.deg_extra, degs.data() + locked);
+      std::vector<int> ord(nact);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const int32_t da = degs[locked + a], db = degs[locked + b];
+        if (da != db) return da < db;
+        return rz[locked + a] < rz[locked + b];
+      });
+      bool ident = true;
+      for (int64_t k = 0; k < nact; ++k) ident = ident && ord[k] == k;
+      if (!ident) {
+        std::vector<int32_t> d2(nact);
+        std::vector<double> z2(nact), s2(nact);
+        for (int64_t k = 0; k < nact; ++k) {
+          d2[k] = degs[locked + ord[k]];
+          z2[k] = rz[locked + ord[k]];
+          s2[k] = rs[locked + ord[k]];
+        }
+        std::copy(d2.begin(), d2.end(), degs.begin() + locked);
+        std::copy(z2.begin(), z2.end(), rz.begin() + locked);
+        std::copy(s2.begin(), s2.end(), rs.begin() + locked);
+        CK(cudaMemcpyAsync(c->perm_d, ord.data(), nact * sizeof(int), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->W, N));
+        CK(gather_cols(c->stream, N, nact, c->W, N, c->perm_d, C + locked * ldv, ldv));
+        CK(cudaStreamSynchronize(c->stream));  // ord is a stack buffer
+      }
+    }
+  }
+  if (S.iter == 1) {
+    std::vector<double> lam(ne, S.mu_1);
+    S.cond = chase_cond_est(lam.data(), degs.data(), ne, locked, S.cc, S.ee);
+  } else {
+    S.cond = chase_cond_est(rz.data(), degs.data(), ne, locked, S.cc, S.ee);
+  }
+  return CHASE_OK;
+}
+
+void solve_count_filter(SolveState& S) {
+  int64_t mv = 0;
+  for (int64_t j = S.locked; j < S.c->ne; ++j) mv += S.degs[j];
+  S.st.matvecs += mv;
+  if (S.mixed) S.st.matvecs_mixed += mv;
+}
+
+int solve_filter(SolveState& S) {
+  LaunchTally tally(S);
+  chase_ctx* c = S.c;
+  const int prec = S.mixed ? CHASE_MIXED_BF16X3 : CHASE_FP64;
+  RC(filter_impl(c, S.A, S.lda, S.C + S.locked * S.ldv, S.ldv, c->ne - S.locked,
+                 S.degs.data() + S.locked, S.cc, S.ee, S.mu_1, prec, &S.st.ms_filter));
+  solve_count_filter(S);
+  return CHASE_OK;
+}
+
+int solve_complete(SolveState& S) {
+  LaunchTally tally(S);
+  chase_ctx* c = S.c;
+  const chase_params& P = c->p;
+  const int64_t N = c->N, ne = c->ne, nev = P.nev, locked = S.locked, nact = ne - locked;
+  double2* C = S.C;
+  const int64_t ldv = S.ldv;
+  int32_t variant = 0;
+  {
+    PhaseTimer tm(c, &S.st.ms_qr);
+    RC(qr_impl(c, C, ldv, ne, S.cond, &variant));
+    CK(copy_cols(c->stream, N, locked, c->V2, N, C, ldv));                       // C[:, :locked] = C2
+    CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
+  }
+  if (variant >= 1 && variant <= 4) S.st.qr_variant_count[variant]++;
+  {
+    PhaseTimer tm(c, &S.st.ms_rr);
+    RC(rr_impl(c, S.A, S.lda, c->V2 + locked * N, N, C + locked * ldv, ldv, nact,
+               S.ritz + locked, &S.st));
+    CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
+  }
+  {
+    PhaseTimer tm(c, &S.st.ms_resid);
+    RC(resid_impl(c, S.A, S.lda, C + locked * ldv, ldv, S.ritz + locked, nact,
+                  S.resid + locked));
+  }
+  double* rz_pin = c->host;
+  double* rs_pin = c->host + ne;
+  CK(cudaMemcpyAsync(rz_pin, S.ritz + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(rs_pin, S.resid + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::copy(rz_pin, rz_pin + nact, S.rz.begin() + locked);
+  std::copy(rs_pin, rs_pin + nact, S.rs.begin() + locked);
+  int64_t nc = 0;
+  while (locked + nc < ne && S.rs[locked + nc] <= S.tol_abs) ++nc;
+  // precision switch (reading of the mixed-precision policy): leave the
+  // reduced-precision filter once the largest residual among the wanted active
+  // pairs reaches switch_tol, or stops falling by at least 3x per iteration.
+  if (S.mixed) {
+    double rmax = 0.0;
+    for (int64_t j = locked + nc; j < nev; ++j) rmax = std::max(rmax, S.rs[j] / S.norm_est);
+    if (rmax <= P.switch_tol || rmax > S.rmax_prev / 3.0) {
+      S.mixed = false;
+      S.st.switch_iter = S.iter;
+    }
+    S.rmax_prev = rmax;
+  }
+  S.locked += nc;
+  ++S.iter;
+  return CHASE_OK;
+}
+
+int solve_end(SolveState& S, chase_stats* stats) {
+  chase_ctx* c = S.c;
+  const long long l0 = launch_count();
+  const int64_t N = c->N, nev = c->p.nev, locked = S.locked;
+  double2* C = S.C;
+  const int64_t ldv = S.ldv;
+  // Output: the first nev Ritz pairs in ascending order (Alg. 2 "Return").
+  const int64_t nsort = std::max<int64_t>(locked, nev);
+  std::vector<int> ord(nsort);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return S.rz[a] < S.rz[b]; });
+  bool ident = true;
+  for (int64_t k = 0; k < nev; ++k) ident = ident && ord[k] == k;
+  if (!ident) {
+    std::vector<double> z2(nev), s2(nev);
+    for (int64_t k = 0; k < nev; ++k) {
+      z2[k] = S.rz[ord[k]];
+      s2[k] = S.rs[ord[k]];
+    }
+    CK(cudaMemcpyAsync(c->perm_d, ord.data(), nev * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(copy_cols(c->stream, N, nsort, C, ldv, c->W, N));
+    CK(gather_cols(c->stream, N, nev, c->W, N, c->perm_d, C, ldv));
+    CK(cudaMemcpyAsync(S.ritz, z2.data(), nev * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(S.resid, s2.data(), nev * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
+  S.launches += launch_count() - l0;
+  CK(cudaEventRecord(S.t_end, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, S.t_start, S.t_end);
+  S.st.ms_total = ms;
+  S.st.iters = S.iter - 1;
+  S.st.locked = (int32_t)locked;
+  S.st.filter_flops = 8.0 * (double)N * (double)N * (double)S.st.matvecs;
+  S.st.kernel_launches = S.launches;
+  if (stats) *stats = S.st;
+  return locked >= nev ? CHASE_OK : CHASE_ERR_NOT_CONVERGED;
+}
+
+}  // namespace chase
+
 // ======================================================================= ABI
 extern "C" {
 
@@ -685,192 +930,15 @@ int chase_residuals(chase_ctx* c, const chase_c128* A, int64_t lda, const chase_
 int chase_solve(chase_ctx* c, const chase_c128* Ac, int64_t lda, chase_c128* Vc, int64_t ldv,
                 const chase_c128* lanczos_start, int64_t ldl, double* ritz, double* resid,
                 chase_stats* stats) {
-  if (!c || !Ac || !Vc || !ritz || !resid || lda < c->N || ldv < c->N)
-    return CHASE_ERR_INVALID_ARG;
-  if (lanczos_start && ldl < c->N) return CHASE_ERR_INVALID_ARG;
-  if (!lanczos_start && c->p.lanczos_vecs > c->ne) return CHASE_ERR_INVALID_ARG;
-  const chase_params& P = c->p;
-  const int64_t N = c->N, ne = c->ne, nev = P.nev;
-  const double2* A = reinterpret_cast<const double2*>(Ac);
-  double2* C = reinterpret_cast<double2*>(Vc);
-  chase_stats st;
-  std::memset(&st, 0, sizeof(st));
-  cudaEvent_t t_start = nullptr, t_end = nullptr;
-  struct EventGuard {  // released on every return path
-    cudaEvent_t* a;
-    cudaEvent_t* b;
-    ~EventGuard() {
-      if (*a) cudaEventDestroy(*a);
-      if (*b) cudaEventDestroy(*b);
-    }
-  } event_guard{&t_start, &t_end};
-  CK(cudaEventCreate(&t_start));
-  CK(cudaEventCreate(&t_end));
-  CK(cudaEventRecord(t_start, c->stream));
-  const long long launches0 = launch_count();
-
-  if (P.fp64_tensor) {  // digits of A once for every tensor-core FP64 product of this solve
-    c->oz_a_valid = false;
-    RC(prepare_a(c, A, lda));
-    c->oz_a_valid = true;
+  SolveState S;
+  RC(solve_begin(S, c, reinterpret_cast<const double2*>(Ac), lda, reinterpret_cast<double2*>(Vc),
+                 ldv, reinterpret_cast<const double2*>(lanczos_start), ldl, ritz, resid));
+  while (solve_active(S)) {
+    RC(solve_prepare(S));
+    RC(solve_filter(S));
+    RC(solve_complete(S));
   }
-  struct ResetDigits {
-    chase_ctx* c;
-    ~ResetDigits() { c->oz_a_valid = false; }
-  } reset_digits{c};
-  double b4[4];
-  {
-    PhaseTimer tm(c, &st.ms_lanczos);
-    const double2* Q0 = lanczos_start ? reinterpret_cast<const double2*>(lanczos_start) : C;
-    const int64_t ldq = lanczos_start ? ldl : ldv;
-    RC(lanczos_impl(c, A, lda, Q0, ldq, P.lanczos_vecs, b4));
-  }
-  const double b_sup = b4[0];
-  double mu_1 = b4[1], mu_ne = b4[2];
-  const double norm_est = b4[3];
-  st.b_sup = b_sup;
-  st.mu_1 = mu_1;
-  st.mu_ne = mu_ne;
-  st.norm_est = norm_est;
-  const double tol_abs = P.tol * norm_est;
-
-  std::vector<int32_t> degs(ne, P.deg_init);
-  std::vector<double> rz(ne, 0.0), rs(ne, 0.0);
-  std::vector<int> perm(ne);
-  double* rz_pin = c->host;
-  double* rs_pin = c->host + ne;
-  int64_t locked = 0;
-  int iter = 1;
-  double cc = (b_sup + mu_ne) / 2.0, ee = (b_sup - mu_ne) / 2.0;
-  bool mixed = P.precision == CHASE_MIXED_BF16X3;
-  double rmax_prev = 1e300;
-  st.switch_iter = mixed ? -1 : 0;
-
-  while (locked < nev && iter <= P.max_iter) {
-    const int64_t nact = ne - locked;
-    if (iter != 1) {
-      mu_1 = *std::min_element(rz.begin(), rz.end());
-      mu_ne = *std::max_element(rz.begin(), rz.end());
-      cc = (b_sup + mu_ne) / 2.0;
-      ee = (b_sup - mu_ne) / 2.0;
-      if (P.deg_opt) {
-        chase_degree_opt(rs.data() + locked, rz.data() + locked, nact, cc, ee, tol_abs, P.deg_max,
-                         P.deg_extra, degs.data() + locked);
-        std::vector<int> ord(nact);
-        std::iota(ord.begin(), ord.end(), 0);
-        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-          const int32_t da = degs[locked + a], db = degs[locked + b];
-          if (da != db) return da < db;
-          return rz[locked + a] < rz[locked + b];
-        });
-        bool ident = true;
-        for (int64_t k = 0; k < nact; ++k) ident = ident && ord[k] == k;
-        if (!ident) {
-          std::vector<int32_t> d2(nact);
-          std::vector<double> z2(nact), s2(nact);
-          for (int64_t k = 0; k < nact; ++k) {
-            d2[k] = degs[locked + ord[k]];
-            z2[k] = rz[locked + ord[k]];
-            s2[k] = rs[locked + ord[k]];
-          }
-          std::copy(d2.begin(), d2.end(), degs.begin() + locked);
-          std::copy(z2.begin(), z2.end(), rz.begin() + locked);
-          std::copy(s2.begin(), s2.end(), rs.begin() + locked);
-          CK(cudaMemcpyAsync(c->perm_d, ord.data(), nact * sizeof(int), cudaMemcpyHostToDevice,
-                             c->stream));
-          CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->W, N));
-          CK(gather_cols(c->stream, N, nact, c->W, N, c->perm_d, C + locked * ldv, ldv));
-          CK(cudaStreamSynchronize(c->stream));  // ord is a stack buffer
-        }
-      }
-    }
-    double cond;
-    if (iter == 1) {
-      std::vector<double> lam(ne, mu_1);
-      cond = chase_cond_est(lam.data(), degs.data(), ne, locked, cc, ee);
-    } else {
-      cond = chase_cond_est(rz.data(), degs.data(), ne, locked, cc, ee);
-    }
-    const int prec = mixed ? CHASE_MIXED_BF16X3 : CHASE_FP64;
-    RC(filter_impl(c, A, lda, C + locked * ldv, ldv, nact, degs.data() + locked, cc, ee, mu_1,
-                   prec, &st.ms_filter));
-    int64_t mv = 0;
-    for (int64_t j = locked; j < ne; ++j) mv += degs[j];
-    st.matvecs += mv;
-    if (mixed) st.matvecs_mixed += mv;
-    int32_t variant = 0;
-    {
-      PhaseTimer tm(c, &st.ms_qr);
-      RC(qr_impl(c, C, ldv, ne, cond, &variant));
-      CK(copy_cols(c->stream, N, locked, c->V2, N, C, ldv));                       // C[:, :locked] = C2
-      CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
-    }
-    if (variant >= 1 && variant <= 4) st.qr_variant_count[variant]++;
-    {
-      PhaseTimer tm(c, &st.ms_rr);
-      RC(rr_impl(c, A, lda, c->V2 + locked * N, N, C + locked * ldv, ldv, nact, ritz + locked,
-                 &st));
-      CK(copy_cols(c->stream, N, nact, C + locked * ldv, ldv, c->V2 + locked * N, N));
-    }
-    {
-      PhaseTimer tm(c, &st.ms_resid);
-      RC(resid_impl(c, A, lda, C + locked * ldv, ldv, ritz + locked, nact, resid + locked));
-    }
-    CK(cudaMemcpyAsync(rz_pin, ritz + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaMemcpyAsync(rs_pin, resid + locked, nact * sizeof(double), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    std::copy(rz_pin, rz_pin + nact, rz.begin() + locked);
-    std::copy(rs_pin, rs_pin + nact, rs.begin() + locked);
-    int64_t nc = 0;
-    while (locked + nc < ne && rs[locked + nc] <= tol_abs) ++nc;
-    // precision switch (reading of the mixed-precision policy): leave the
-    // reduced-precision filter once the largest residual among the wanted active
-    // pairs reaches switch_tol, or stops falling by at least 3x per iteration.
-    if (mixed) {
-      double rmax = 0.0;
-      for (int64_t j = locked + nc; j < nev; ++j) rmax = std::max(rmax, rs[j] / norm_est);
-      if (rmax <= P.switch_tol || rmax > rmax_prev / 3.0) {
-        mixed = false;
-        st.switch_iter = iter;
-      }
-      rmax_prev = rmax;
-    }
-    locked += nc;
-    ++iter;
-  }
-  // Output: the first nev Ritz pairs in ascending order (Alg. 2 "Return").
-  const int64_t nsort = std::max<int64_t>(locked, nev);
-  std::vector<int> ord(nsort);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return rz[a] < rz[b]; });
-  bool ident = true;
-  for (int64_t k = 0; k < nev; ++k) ident = ident && ord[k] == k;
-  if (!ident) {
-    std::vector<double> z2(nev), s2(nev);
-    for (int64_t k = 0; k < nev; ++k) {
-      z2[k] = rz[ord[k]];
-      s2[k] = rs[ord[k]];
-    }
-    CK(cudaMemcpyAsync(c->perm_d, ord.data(), nev * sizeof(int), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(copy_cols(c->stream, N, nsort, C, ldv, c->W, N));
-    CK(gather_cols(c->stream, N, nev, c->W, N, c->perm_d, C, ldv));
-    CK(cudaMemcpyAsync(ritz, z2.data(), nev * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(resid, s2.data(), nev * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  }
-  CK(cudaEventRecord(t_end, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, t_start, t_end);
-  st.ms_total = ms;
-  st.iters = iter - 1;
-  st.locked = (int32_t)locked;
-  st.filter_flops = 8.0 * (double)N * (double)N * (double)st.matvecs;
-  st.kernel_launches = launch_count() - launches0;
-  if (stats) *stats = st;
-  return locked >= nev ? CHASE_OK : CHASE_ERR_NOT_CONVERGED;
+  return solve_end(S, stats);
 }
 
 }  // extern "C"

@@ -48,4 +48,47 @@ int ctx_prepare_a(chase_ctx* c, const double2* A, int64_t lda);
 // or unscaled recurrence; al and be get dmax + 1 entries.
 void cheb_coefficients(int dmax, double c, double e, double mu1, bool scaled,
                        std::vector<double>& al, std::vector<double>& be);
+
+// One solve of Alg. 2 as resumable phases, so that a batch of problems can
+// advance in lockstep and share the filter launches (chase_solve_batch);
+// chase_solve runs the same phases in a loop.
+struct SolveState {
+  chase_ctx* c = nullptr;
+  const double2* A = nullptr;
+  int64_t lda = 0;
+  double2* C = nullptr;
+  int64_t ldv = 0;
+  double* ritz = nullptr;
+  double* resid = nullptr;
+  chase_stats st{};
+  cudaEvent_t t_start = nullptr, t_end = nullptr;
+  long long launches = 0;  // kernels launched by this solve's phases (on any thread)
+  double b_sup = 0, mu_1 = 0, mu_ne = 0, norm_est = 0, tol_abs = 0, cc = 0, ee = 0;
+  double rmax_prev = 1e300, cond = 0;
+  std::vector<int32_t> degs;
+  std::vector<double> rz, rs;
+  int64_t locked = 0;
+  int iter = 1;
+  bool mixed = false;
+  SolveState() = default;
+  SolveState(const SolveState&) = delete;
+  SolveState& operator=(const SolveState&) = delete;
+  ~SolveState();
+};
+// Validation, digits of A, Lanczos bounds (Alg. 2 first line).
+int solve_begin(SolveState& S, chase_ctx* c, const double2* A, int64_t lda, double2* C,
+                int64_t ldv, const double2* Q0, int64_t ldq, double* ritz, double* resid);
+// locked < nev and iter <= max_iter (Alg. 2 loop test)
+bool solve_active(const SolveState& S);
+// Bounds update, degreeOpt and sort of the active columns, CondEst.
+int solve_prepare(SolveState& S);
+// The filter of the active columns with this problem's own launches.
+int solve_filter(SolveState& S);
+// MatVec accounting of one filter phase (solve_filter calls it).
+void solve_count_filter(SolveState& S);
+// QR, restore of the locked columns, Rayleigh-Ritz, residuals, locking,
+// precision switch; advances the iteration.
+int solve_complete(SolveState& S);
+// Output order (Alg. 2 "Return") and statistics; returns the solve's status.
+int solve_end(SolveState& S, chase_stats* stats);
 }  // namespace chase

@@ -38,10 +38,19 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "mixed.cuh"
 
 namespace chase {
+#define RC_M(call)                     \
+  do {                                 \
+    const int _rc = (call);            \
+    if (_rc != CHASE_OK) return _rc;   \
+  } while (0)
 namespace {
 
 // K block of 32 BF16 (64-byte rows, 64B swizzle) and a 4-stage ring: three
@@ -67,6 +76,7 @@ struct Params {
   __nv_bfloat16* Bn_hi;         // next-step operand planes (rows = B^T rows, ld = 2 Np)
   __nv_bfloat16* Bn_lo;
   int write_next;
+  int group;                    // row blocks per sweep of the grouped raster order
   int* err;
 };
 
@@ -178,11 +188,13 @@ __device__ __forceinline__ void split2f(float x, __nv_bfloat16& hi, __nv_bfloat1
 __device__ __forceinline__ int64_t brow_re(int64_t j) { return (j >> 7) * 256 + (j & 127); }
 
 // ---------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(NTHREADS, 1)
-    mixed_filter_kernel(const __grid_constant__ CUtensorMap tmAh,
-                        const __grid_constant__ CUtensorMap tmAl,
-                        const __grid_constant__ CUtensorMap tmBh,
-                        const __grid_constant__ CUtensorMap tmBl, Params P) {
+// One 128 x 256 output tile (row block rb, column tile ct of the active
+// columns) of one filter step; the per-problem kernel and the grouped kernel
+// (many problems in one launch) both run it.
+__device__ __forceinline__ void mixed_tile(const CUtensorMap* tmAh, const CUtensorMap* tmAl,
+                                           const CUtensorMap* tmBh, const CUtensorMap* tmBl,
+                                           const Params& P, unsigned rb, unsigned ct,
+                                           bool maps_in_global) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment of the shared-window address (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -193,8 +205,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
-  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, 16, rb, ct);
   const int64_t m0 = (int64_t)rb * TM;
   const int64_t tile = (P.j0 >> 7) + ct;          // absolute 128-column tile
   const int nkb = (int)((2 * P.Np) / TK);
@@ -226,6 +236,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------- TMA producer
+    if (maps_in_global) {  // tensor maps read from global memory by the TMA unit
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmAh) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmAl) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmBh) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmBl) : "memory");
+    }
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
@@ -239,10 +255,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint8_t* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(full, STAGE_BYTES);
       const int kx = kb * TK;
-      tma_load_2d(smem_u32(st), &tmAh, kx, (int)m0, full);
-      tma_load_2d(smem_u32(st + A_TILE), &tmAl, kx, (int)m0, full);
-      tma_load_2d(smem_u32(st + 2 * A_TILE), &tmBh, kx, (int)(tile * TN), full);
-      tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), &tmBl, kx, (int)(tile * TN), full);
+      tma_load_2d(smem_u32(st), tmAh, kx, (int)m0, full);
+      tma_load_2d(smem_u32(st + A_TILE), tmAl, kx, (int)m0, full);
+      tma_load_2d(smem_u32(st + 2 * A_TILE), tmBh, kx, (int)(tile * TN), full);
+      tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), tmBl, kx, (int)(tile * TN), full);
       ++issued;
     }
     // drain: every issued stage must land before the CTA may exit
@@ -368,6 +384,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  "r"(TMEM_COLS)
                  : "memory");
   }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mixed_filter_kernel(const __grid_constant__ CUtensorMap tmAh,
+                        const __grid_constant__ CUtensorMap tmAl,
+                        const __grid_constant__ CUtensorMap tmBh,
+                        const __grid_constant__ CUtensorMap tmBl, Params P) {
+  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
+  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, P.group, rb, ct);
+  mixed_tile(&tmAh, &tmAl, &tmBh, &tmBl, P, rb, ct, false);
+}
+
+// Many problems' filter steps in one launch: entry p of the table holds problem
+// p's tensor maps, step parameters and first CTA index; CTA id looks up its
+// problem (binary search on the first indices) and runs that problem's tile
+// id - first in the same raster order as the per-problem launch, so every
+// problem's results are those of its own launch.
+struct alignas(64) GroupEntry {
+  CUtensorMap ah, al, bh, bl;
+  Params P;
+  int first, nrow, ncol, pad;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mixed_filter_grouped_kernel(const GroupEntry* __restrict__ tab, int count) {
+  const int id = (int)blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last entry with first <= id
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].first <= id) lo = mid;
+    else hi = mid - 1;
+  }
+  const GroupEntry* e = tab + lo;
+  const Params P = e->P;
+  unsigned rb, ct;
+  grouped_tile((unsigned)(id - e->first), (unsigned)e->nrow, (unsigned)e->ncol, P.group, rb, ct);
+  mixed_tile(&e->ah, &e->al, &e->bh, &e->bl, P, rb, ct, true);
 }
 
 // ----------------------------------------------------------- conversions
@@ -515,65 +568,263 @@ void mixed_free(MixedWork& w) {
   w = MixedWork{};
 }
 
-int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, double2* V,
-                 int64_t ldv, int64_t ncols, const int32_t* degs, double c, const double* al,
-                 const double* be, double2* W, int64_t ldw, MixedWork& w) {
-  if (ncols == 0) return CHASE_OK;
-  if (!w.maps || N != w.N || ncols > w.ne) return CHASE_ERR_INVALID_ARG;
-  const Maps* maps = static_cast<const Maps*>(w.maps);
+namespace {
+// Operand planes of A and of Y_0 = V (into operand buffer 0 and FP32 state 0).
+void mixed_prologue(cudaStream_t s, int64_t N, const double2* A, int64_t lda, const double2* V,
+                    int64_t ldv, int64_t ncols, MixedWork& w) {
   const int64_t Np = cdiv(N, KPAD) * KPAD;
-  const int64_t brows = cdiv(w.ne, 128) * 256;
-  const size_t b_elems = (size_t)brows * 2 * Np;
-  __nv_bfloat16* Yh = static_cast<__nv_bfloat16*>(w.Yhi);
-  __nv_bfloat16* Yl = static_cast<__nv_bfloat16*>(w.Ylo);
-  // planes of A, then of Y_0 = V into operand buffer 0
   split_a_kernel<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(N, 32), 1), dim3(32, 8, 1), 0, s>>>(
       N, Np, A, lda, static_cast<__nv_bfloat16*>(w.Ahi), static_cast<__nv_bfloat16*>(w.Alo));
   count_launch();
+  split_y_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(
+      N, Np, 0, V, ldv, static_cast<__nv_bfloat16*>(w.Yhi), static_cast<__nv_bfloat16*>(w.Ylo),
+      static_cast<float2*>(w.S32));
+  count_launch();
+}
+
+// Parameters of filter step i (1-based) and the operand-plane buffer it reads.
+Params step_params(int64_t N, int64_t ncols, const int32_t* degs, double c, const double* al,
+                   const double* be, int i, int group, MixedWork& w, int* bin_out) {
+  const int64_t Np = cdiv(N, KPAD) * KPAD;
+  const int64_t brows = cdiv(w.ne, 128) * 256;
+  const size_t b_elems = (size_t)brows * 2 * Np;
   float2* st[2] = {static_cast<float2*>(w.S32), static_cast<float2*>(w.S32) + (size_t)N * w.ne};
-  split_y_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, Np, 0, V, ldv,
-                                                                                   Yh, Yl, st[0]);
-  count_launch();
-  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_CUDA_FAIL();
-  (void)W;
-  (void)ldw;
   const int dmax = degs[ncols - 1];
-  for (int i = 1; i <= dmax; ++i) {
-    const int64_t j0 = std::lower_bound(degs, degs + ncols, i) - degs;
-    const int src = (i - 1) & 1, dst = i & 1;   // FP32 state buffers
-    const int bin = (i - 1) & 1, bout = i & 1;  // operand plane buffers
-    Params P;
-    P.N = N;
-    P.Np = Np;
-    P.j0 = j0;
-    P.ncols = ncols;
-    P.Ycur = st[src];
-    P.Yprev = st[dst];
-    P.alpha = (float)al[i];
-    P.beta = (i == 1) ? 0.0f : (float)be[i];
-    P.gamma = (float)c;
-    P.Bn_hi = Yh + bout * b_elems;
-    P.Bn_lo = Yl + bout * b_elems;
-    P.write_next = i < dmax;
-    P.err = w.err;
-    const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols - 1) / 128 - j0 / 128 + 1), 1);
-    mixed_filter_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->ah, maps->al, maps->bh[bin],
-                                                           maps->bl[bin], P);
+  const int src = (i - 1) & 1, dst = i & 1;   // FP32 state buffers
+  const int bout = i & 1;                      // operand plane buffer written
+  Params P;
+  P.N = N;
+  P.Np = Np;
+  P.j0 = std::lower_bound(degs, degs + ncols, i) - degs;
+  P.ncols = ncols;
+  P.Ycur = st[src];
+  P.Yprev = st[dst];
+  P.alpha = (float)al[i];
+  P.beta = (i == 1) ? 0.0f : (float)be[i];
+  P.gamma = (float)c;
+  P.Bn_hi = static_cast<__nv_bfloat16*>(w.Yhi) + bout * b_elems;
+  P.Bn_lo = static_cast<__nv_bfloat16*>(w.Ylo) + bout * b_elems;
+  P.write_next = i < dmax;
+  P.group = group;
+  P.err = w.err;
+  *bin_out = (i - 1) & 1;
+  return P;
+}
+
+unsigned step_col_tiles(const Params& P) {
+  return (unsigned)((P.ncols - 1) / 128 - P.j0 / 128 + 1);
+}
+
+// ----------------------------------------------- raster-order autotuner
+// The grouped raster order (`group` row blocks per sweep of the column tiles)
+// decides how many CTAs resident at one time share A's planes and the operand
+// planes in L2; the best group depends on N, on the number of column tiles and
+// on the device. The first filter call for a shape (per device, N, column
+// tiles) times filter step 1 with each candidate (step 1 reads only the start
+// block and ignores the state it overwrites, so repeating it changes nothing)
+// and keeps the fastest; later calls reuse it. The arithmetic of a tile does
+// not depend on the order, so the choice never changes a result.
+constexpr int kGroupCandidates[] = {4, 8, 16, 32};
+constexpr int kDefaultGroup = 16;
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int64_t, unsigned>, int> g_tuned_group;
+
+int tuned_group(int64_t N, unsigned coltiles) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tuned_group.find(std::make_tuple(dev, N, coltiles));
+  return it == g_tuned_group.end() ? 0 : it->second;
+}
+
+int tune_group(cudaStream_t s, const Maps* maps, Params P, dim3 grid) {
+  const int cached = tuned_group(P.N, grid.y);
+  if (cached) return cached;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return kDefaultGroup;
+  int best = kDefaultGroup;
+  float best_ms = 1e30f;
+  for (int g : kGroupCandidates) {
+    P.group = g;
+    cudaEventRecord(e0, s);
+    mixed_filter_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->ah, maps->al, maps->bh[0],
+                                                           maps->bl[0], P);
     count_launch();
-    if (cudaGetLastError() != cudaSuccess) return CHASE_CUDA_FAIL();
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = g;
+    }
   }
-  // even degrees: every column's final value is in state buffer 0
-  state_to_f64_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(N, st[0], V,
-                                                                                       ldv);
-  count_launch();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned_group[std::make_tuple(dev, P.N, grid.y)] = best;
+  return best;
+}
+
+int check_err(cudaStream_t s, int* err) {
   int herr = 0;
-  if (cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return CHASE_CUDA_FAIL();
   if (herr != 0) {
     fprintf(stderr, "[chase] tensor-core filter: pipeline wait expired (code %d)\n", herr);
     return CHASE_CUDA_FAIL();
   }
+  return CHASE_OK;
+}
+}  // namespace
+
+int mixed_filter(cudaStream_t s, int64_t N, const double2* A, int64_t lda, double2* V,
+                 int64_t ldv, int64_t ncols, const int32_t* degs, double c, const double* al,
+                 const double* be, double2* W, int64_t ldw, MixedWork& w, bool autotune) {
+  if (ncols == 0) return CHASE_OK;
+  if (!w.maps || N != w.N || ncols > w.ne) return CHASE_ERR_INVALID_ARG;
+  (void)W;
+  (void)ldw;
+  const Maps* maps = static_cast<const Maps*>(w.maps);
+  mixed_prologue(s, N, A, lda, V, ldv, ncols, w);
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CHASE_CUDA_FAIL();
+  const int dmax = degs[ncols - 1];
+  int group = kDefaultGroup;
+  for (int i = 1; i <= dmax; ++i) {
+    int bin = 0;
+    Params P = step_params(N, ncols, degs, c, al, be, i, group, w, &bin);
+    const dim3 grid((unsigned)cdiv(N, TM), step_col_tiles(P), 1);
+    if (i == 1 && autotune) P.group = group = tune_group(s, maps, P, grid);
+    mixed_filter_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->ah, maps->al, maps->bh[bin],
+                                                           maps->bl[bin], P);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return CHASE_CUDA_FAIL();
+  }
+  // even degrees: every column's final value is in state buffer 0
+  state_to_f64_kernel<<<dim3((unsigned)cdiv(N, 256), (unsigned)ncols, 1), 256, 0, s>>>(
+      N, static_cast<const float2*>(w.S32), V, ldv);
+  count_launch();
+  return check_err(s, w.err);
+}
+
+cudaError_t mixed_group_reserve(MixedGroupTable& t, size_t entries) {
+  if (entries <= t.capacity) return cudaSuccess;
+  mixed_group_free(t);
+  cudaError_t e;
+  if ((e = cudaMalloc(&t.dev, entries * sizeof(GroupEntry))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&t.host, entries * sizeof(GroupEntry))) != cudaSuccess) return e;
+  t.capacity = entries;
+  return cudaSuccess;
+}
+
+void mixed_group_free(MixedGroupTable& t) {
+  if (t.dev) cudaFree(t.dev);
+  if (t.host) cudaFreeHost(t.host);
+  t = MixedGroupTable{};
+}
+
+size_t mixed_group_entries(int count, const MixedGroupItem* items) {
+  size_t n = 0;
+  for (int k = 0; k < count; ++k)
+    if (items[k].ncols > 0) n += (size_t)items[k].degs[items[k].ncols - 1];
+  return n;
+}
+
+int mixed_filter_grouped(cudaStream_t s, int count, const MixedGroupItem* items,
+                         MixedGroupTable& t, int* launches) {
+  static std::once_flag attr_once[kMaxDevices];
+  once_per_device(attr_once, []() {
+    cudaFuncSetAttribute(mixed_filter_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+  });
+  int dmax_all = 0;
+  for (int k = 0; k < count; ++k) {
+    const MixedGroupItem& it = items[k];
+    if (it.ncols == 0) continue;
+    if (!it.w || !it.w->maps || it.N != it.w->N || it.ncols > it.w->ne)
+      return CHASE_ERR_INVALID_ARG;
+    dmax_all = std::max(dmax_all, (int)it.degs[it.ncols - 1]);
+  }
+  if (dmax_all == 0) return CHASE_OK;
+  if (mixed_group_entries(count, items) > t.capacity) return CHASE_ERR_INVALID_ARG;
+  // operand planes of every problem, then the step table: for step i the
+  // entries of the problems still filtering, with their first CTA indices
+  for (int k = 0; k < count; ++k) {
+    const MixedGroupItem& it = items[k];
+    if (it.ncols == 0) continue;
+    mixed_prologue(s, it.N, it.A, it.lda, it.V, it.ldv, it.ncols, *it.w);
+    if (cudaMemsetAsync(it.w->err, 0, sizeof(int), s) != cudaSuccess) return CHASE_CUDA_FAIL();
+  }
+  GroupEntry* host = static_cast<GroupEntry*>(t.host);
+  std::vector<size_t> off(dmax_all + 2, 0);
+  std::vector<int> ctas(dmax_all + 1, 0);
+  size_t n = 0;
+  for (int i = 1; i <= dmax_all; ++i) {
+    off[i] = n;
+    int first = 0;
+    for (int k = 0; k < count; ++k) {
+      const MixedGroupItem& it = items[k];
+      if (it.ncols == 0 || it.degs[it.ncols - 1] < i) continue;
+      const Maps* maps = static_cast<const Maps*>(it.w->maps);
+      const int g = tuned_group(it.N, (unsigned)((it.ncols - 1) / 128 + 1));
+      int bin = 0;
+      GroupEntry& e = host[n++];
+      e.P = step_params(it.N, it.ncols, it.degs, it.c, it.al, it.be, i,
+                        g ? g : kDefaultGroup, *it.w, &bin);
+      e.ah = maps->ah;
+      e.al = maps->al;
+      e.bh = maps->bh[bin];
+      e.bl = maps->bl[bin];
+      e.nrow = (int)cdiv(it.N, TM);
+      e.ncol = (int)step_col_tiles(e.P);
+      e.first = first;
+      e.pad = 0;
+      first += e.nrow * e.ncol;
+    }
+    ctas[i] = first;
+  }
+  off[dmax_all + 1] = n;
+  if (cudaMemcpyAsync(t.dev, host, n * sizeof(GroupEntry), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return CHASE_CUDA_FAIL();
+  // the degree steps of all problems as one CUDA graph: one grouped launch per step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return CHASE_CUDA_FAIL();
+  const GroupEntry* dev = static_cast<const GroupEntry*>(t.dev);
+  for (int i = 1; i <= dmax_all; ++i) {
+    mixed_filter_grouped_kernel<<<(unsigned)ctas[i], NTHREADS, SMEM_BYTES, s>>>(
+        dev + off[i], (int)(off[i + 1] - off[i]));
+    count_launch();
+  }
+  const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (ce != cudaSuccess || !graph) return CHASE_CUDA_FAIL();
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return CHASE_CUDA_FAIL();
+  const cudaError_t le = cudaGraphLaunch(exec, s);
+  if (le != cudaSuccess) {
+    cudaGraphExecDestroy(exec);
+    return CHASE_CUDA_FAIL();
+  }
+  if (launches) *launches = dmax_all;
+  for (int k = 0; k < count; ++k) {
+    const MixedGroupItem& it = items[k];
+    if (it.ncols == 0) continue;
+    state_to_f64_kernel<<<dim3((unsigned)cdiv(it.N, 256), (unsigned)it.ncols, 1), 256, 0, s>>>(
+        it.N, static_cast<const float2*>(it.w->S32), it.V, it.ldv);
+    count_launch();
+  }
+  const cudaError_t se = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(exec);
+  if (se != cudaSuccess) return CHASE_CUDA_FAIL();
+  for (int k = 0; k < count; ++k)
+    if (items[k].ncols > 0) RC_M(check_err(s, items[k].w->err));
   return CHASE_OK;
 }
 
