@@ -95,6 +95,7 @@ void free_ctx(chase_ctx* c) {
   ozaki_free(c->ow);
   householder_free(c->hw);
   if (c->oz_partial) cudaFree(c->oz_partial);
+  if (c->QRt) cudaFree(c->QRt);
   if (c->gw) cudaFree(c->gw);
   if (c->gd) cudaFree(c->gd);
   if (c->host) cudaFreeHost(c->host);
@@ -229,34 +230,130 @@ int check_degs(const int32_t* degs, int64_t n, int deg_cap) {
 //
 // With the tensor-core FP64 products (fp64_tensor):
 //  * Gram matrix. A digit-sliced X^H X carries an error of about
-//    sqrt(2N) 2^-48 2^(e_i + e_j), where 2^e_i (between 2 and 4 times the
-//    largest entry of column i) is the column's digit scale; FP64 gives about
-//    sqrt(N) 2^-53 of the column norms' product. The orthogonality a pass
-//    delivers is the Gram error times kappa(X)^2. Passes that are not the last
-//    of their variant (the next pass removes their error) use the tensor cores.
-//    The last pass of CholeskyQR2 / shifted CholeskyQR2 (input orthonormal to
-//    about the previous pass's kappa^2 u) uses them when that bound, with the
-//    largest column scale, stays below 1e-13 (the orthogonality target is
-//    1e-12): true for flat columns (a filtered block that mixes many
-//    eigenvectors: 2^e ~ 5 - 10 / sqrt(N), bound ~1e-14), false for localised
-//    ones (nearly converged Ritz vectors with an entry near 1: bound ~1e-11),
-//    which get the FP64 Gram. CholeskyQR1's single pass (kappa up to 20) always
-//    keeps the FP64 Gram.
+//    sqrt(2N) 2^-50 2^(e_i + e_j) from the dropped digit pairs, where 2^e_i
+//    (between 2 and 4 times the largest entry of column i) is the column's
+//    digit scale, plus the rounding of the digits themselves, about
+//    2^(e_i - 48) ||x_j|| + 2^(e_j - 48) ||x_i||. FP64 gives about sqrt(N)
+//    2^-53 of the column norms' product. The orthogonality a pass delivers is
+//    the Gram error times kappa(X)^2. Every pass keeps the level-8 digit pairs
+//    too, which lowers the first term to sqrt(2N) 2^-58 2^(e_i + e_j): with
+//    the plain product a first pass over a block of localised columns (Gram
+//    error near 1e-12) left kappa(X1) large enough for the second pass to
+//    square it into its orthogonality (2e-11 at N = 40000, n = 3000). The last
+//    pass of CholeskyQR2 / shifted CholeskyQR2 (input orthonormal to about the
+//    previous pass's kappa^2 times its Gram error) uses the tensor cores when
+//    2^(emax - 46) + sqrt(2N) 2^(2 emax - 56), with the largest column scale,
+//    stays below 1e-13 (the orthogonality target is 1e-12): true for any
+//    nearly orthonormal block (its entries are at most 1, emax <= 2), flat or
+//    localised. CholeskyQR1's single pass (kappa up to 20) keeps the FP64
+//    Gram.
 //  * X U^-1. When max |U - I| <= 1e-4 (the input is orthonormal to about 1e-4),
 //    X U^-1 = X + X D with D = U^-1 - I, |D| <= ~1e-4: the digit-sliced product
 //    X D carries an error of about sqrt(2n) 2^-44 max|X_i.| max|D_.j|, below
 //    1e-15 absolute, so it runs on the tensor cores (U^-1 by a recursive blocked
-//    inversion with FP64 GEMMs). Otherwise
-//    X U^-1 is the FP64 triangular solve: a digit-sliced product with a general
-//    U^-1, whose columns mix entries of very different size for a filtered
-//    block, would keep the small entries only to 2^-48 of their column's
-//    largest and lose the span of the small columns.
+//    inversion with FP64 GEMMs). Otherwise the solve is a digit-sliced product
+//    with iterative refinement (tensor_trsm below).
 constexpr double kNearIdentity = 1e-4;
 
 constexpr double kGramTol = 1e-13;
 
+// Refinement of T = X U^-1 on the tensor cores. A digit-sliced product with a
+// general U^-1 is accurate to about sqrt(n) 2^-48 of max|X_i.| max|U^-1_.j|,
+// which for a filtered block is kappa(X) times the size of the result: the
+// first product T0 = X U^-1 leaves a relative backward error
+// eta0 = max_j ||X_j - (T0 U)_j|| / ||X_j|| of about sqrt(n) 2^-48 kappa. Each
+// step rounds T to its own digits (so the next product takes it exactly),
+// forms R = X - T U (extended product: the result cancels to eta of X, so the
+// level-8 pairs are kept) and T <- T + R U^-1 in the FP64 epilogue; this
+// multiplies the backward error by about eta0, down to the dropped pairs'
+// sqrt(n) 2^-58 of the scales (the triangular solve in FP64 leaves about
+// sqrt(n) 2^-53). Steps continue
+// while eta_k eta0 > 1e-14 (at most kMaxRefine). The input must stay readable
+// for every step: Xsaved holds a copy of X (the block the QR was given, for
+// the first pass); without it one step is taken, overwriting X with R (passes
+// after the first, whose input is already well conditioned). If the steps
+// do not converge the FP64 triangular solve runs on the saved input.
+constexpr int kMaxRefine = 6;
+constexpr double kRefineTarget = 1e-14;
+
+int tensor_trsm(chase_ctx* c, double2* X, int64_t ldx, int64_t n, const double2* Xsaved) {
+  const int64_t N = c->N;
+  double2* T = c->QRt;
+  double* eta_h = c->host + 2 * c->ne + 9;
+  // U^-1 into Yeig (free during the QR); U itself as a dense operand
+  CK(triangular_inverse(c->stream, n, c->G, c->ne, c->dinv, c->Yeig, c->ne, c->jw.T));
+  CK(zero_lower(c->stream, n, c->G, c->ne));
+  {
+    Epilogue ep{};  // T = X U^-1
+    ep.mode = EPI_STORE;
+    ep.Y = T;
+    ep.ldy = N;
+    CK(ozaki_gemm_general(c->stream, N, n, X, ldx, false, n, c->Yeig, c->ne, ep, c->ow));
+  }
+  const double2* Xin = Xsaved ? Xsaved : X;
+  const int64_t ldin = Xsaved ? N : ldx;
+  double eta0 = -1.0;
+  for (int k = 0;; ++k) {
+    // T to the value its digits represent, so that T U below takes it exactly:
+    // R then carries only the dropped pairs' error, not T's digit rounding
+    // (which would leave a backward error of a few 2^-48 of the rows' scales)
+    CK(ozaki_round_left(c->stream, N, n, T, N, c->ow));
+    {
+      Epilogue ep{};  // R = Xin - T U, into X (X's content is Xin's copy or used last here)
+      ep.mode = EPI_FILTER;
+      ep.alpha = -1.0;
+      ep.gamma = 1.0;
+      ep.beta = 0.0;
+      ep.X = Xin;
+      ep.ldx = ldin;
+      ep.Y = X;
+      ep.ldy = ldx;
+      CK(ozaki_gemm_general(c->stream, N, n, T, N, false, n, c->G, c->ne, ep, c->ow, true));
+    }
+    bool last = Xsaved == nullptr;
+    if (!last) {
+      CK(max_col_ratio(c->stream, N, n, X, ldx, Xin, ldin, c->dscal + 2));
+      CK(cudaMemcpyAsync(eta_h, c->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      RC(ozaki_check(c->stream, c->ow));
+      const double eta = *eta_h;
+      if (eta0 < 0.0) eta0 = eta;
+      // steps still needed at the rate eta0 per step: eta0^(k + 2) <= target
+      const bool hopeless =
+          eta0 > 1e-300 && std::log(kRefineTarget) / std::log(eta0) - 2.0 > kMaxRefine - 1;
+      if (!(eta <= 0.5) || hopeless || (k + 1 >= kMaxRefine && eta * eta0 > kRefineTarget)) {
+        // no convergence (or non-finite values): the FP64 solve on the input
+        CK(copy_cols(c->stream, N, n, Xsaved, N, X, ldx));
+        CK(trsm_right_upper(c->stream, N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
+        return CHASE_OK;
+      }
+      last = eta * eta0 <= kRefineTarget;
+    }
+    Epilogue ep{};
+    ep.mode = EPI_FILTER;
+    ep.alpha = 1.0;
+    if (last) {  // X = T + R U^-1 (R's digits are taken before X is written)
+      ep.gamma = -1.0;
+      ep.beta = 0.0;
+      ep.X = T;
+      ep.ldx = N;
+      ep.Y = X;
+      ep.ldy = ldx;
+    } else {     // T <- T + R U^-1
+      ep.gamma = 0.0;
+      ep.beta = 1.0;
+      ep.X = T;
+      ep.ldx = N;
+      ep.Y = T;
+      ep.ldy = N;
+    }
+    CK(ozaki_gemm_general(c->stream, N, n, X, ldx, false, n, c->Yeig, c->ne, ep, c->ow));
+    if (last) return ozaki_check(c->stream, c->ow);
+  }
+}
+
 int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_factor,
-                bool last, bool single, int* info_h) {
+                bool last, bool single, const double2* Xsaved, int* info_h) {
   const bool tensor = c->p.fp64_tensor != 0;
   bool tc = tensor && !single;
   double* dev_h = c->host + 2 * c->ne + 10;
@@ -266,7 +363,7 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
       ep.mode = EPI_STORE;
       ep.Y = c->G;
       ep.ldy = c->ne;
-      CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow));
+      CK(ozaki_gemm_general(c->stream, n, c->N, X, ldx, true, n, X, ldx, ep, c->ow, true));
       CK(hermitian_part(c->stream, n, c->G, c->ne));
       if (last) {  // keep it only if its error bound allows (see above)
         int* emax_h = reinterpret_cast<int*>(c->host + 2 * c->ne + 11);
@@ -274,7 +371,8 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
         CK(cudaMemcpyAsync(emax_h, c->info + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         RC(ozaki_check(c->stream, c->ow));
-        const double bound = std::sqrt(2.0 * (double)c->N) * std::ldexp(1.0, 2 * *emax_h - 48);
+        const double bound = std::ldexp(1.0, *emax_h - 46) +
+                             std::sqrt(2.0 * (double)c->N) * std::ldexp(1.0, 2 * *emax_h - 56);
         tc = bound <= kGramTol;
       }
     }
@@ -309,6 +407,7 @@ int cholqr_pass(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double shift_f
     CK(ozaki_gemm_general(c->stream, c->N, n, X, ldx, false, n, c->Yeig, c->ne, ep, c->ow));
     return ozaki_check(c->stream, c->ow);
   }
+  if (tensor) return tensor_trsm(c, X, ldx, n, Xsaved);
   CK(trsm_right_upper(c->stream, c->N, n, X, ldx, c->G, c->ne, c->dinv, c->info));
   return CHASE_OK;
 }
@@ -323,7 +422,8 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
     const int passes = v == CHASE_QR_CHOLQR1 ? 1 : 2;
     bool ok = true;
     for (int k = 0; k < passes && ok; ++k) {
-      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, passes == 1, info_h));
+      RC(cholqr_pass(c, X, ldx, n, 0.0, k == passes - 1, passes == 1, k == 0 ? c->W : nullptr,
+                     info_h));
       ok = (*info_h == 0);
     }
     if (ok) {
@@ -336,9 +436,9 @@ int qr_impl(chase_ctx* c, double2* X, int64_t ldx, int64_t n, double cond, int32
   }
   // Alg. 4 shifted branch: s = 11 (m n + n (n + 1)) u ||X||_F^2, then CholeskyQR2
   const double factor = 11.0 * ((double)c->N * (double)n + (double)n * (double)(n + 1)) * kU;
-  RC(cholqr_pass(c, X, ldx, n, factor, false, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, false, false, info_h));
-  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, false, info_h));
+  RC(cholqr_pass(c, X, ldx, n, factor, false, false, c->W, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, false, false, nullptr, info_h));
+  if (*info_h == 0) RC(cholqr_pass(c, X, ldx, n, 0.0, true, false, nullptr, info_h));
   if (*info_h == 0) {
     if (variant) *variant = CHASE_QR_SHIFTED;
     return CHASE_OK;
@@ -369,7 +469,8 @@ int rr_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* Q, int64
     eg.mode = EPI_STORE;
     eg.Y = c->G;
     eg.ldy = c->ne;
-    CK(ozaki_gemm_general(c->stream, n, c->N, Q, ldq, true, n, c->W, c->N, eg, c->ow));
+    // extended: the off-diagonal of Q^H A Q cancels to the size of the residuals
+    CK(ozaki_gemm_general(c->stream, n, c->N, Q, ldq, true, n, c->W, c->N, eg, c->ow, true));
   } else {
     CK(zgram(c->stream, c->N, n, n, Q, ldq, c->W, c->N, c->G, c->ne, false, c->gram_ws,
              c->gram_ws_elems));
@@ -437,9 +538,10 @@ int resid_impl(chase_ctx* c, const double2* A, int64_t lda, const double2* V, in
 // Lanczos block product on the tensor cores (digits of A prepared by the caller).
 cudaError_t heev_tensor_gemm(void* vc, int64_t M, int64_t K, const double2* X, int64_t ldx,
                              bool conj_trans, int64_t ncols, const double2* B, int64_t ldb,
-                             const Epilogue& ep) {
+                             const Epilogue& ep, bool extended) {
   chase_ctx* c = static_cast<chase_ctx*>(vc);
-  return ozaki_gemm_general(c->stream, M, K, X, ldx, conj_trans, ncols, B, ldb, ep, c->ow);
+  return ozaki_gemm_general(c->stream, M, K, X, ldx, conj_trans, ncols, B, ldb, ep, c->ow,
+                            extended);
 }
 
 cudaError_t lanczos_tensor_matmul(void* vc, const double2* Q, int64_t ldq, int nvec, double2* W,
@@ -842,6 +944,7 @@ int chase_create(const chase_params* p, void* stream, chase_ctx** out) {
   if (ok && p->fp64_tensor) {
     A(ozaki_alloc(c->ow, N, ne));
     if (ok) A(dalloc(&c->oz_partial, (size_t)cdiv(N, 32) * ne));
+    if (ok) A(dalloc(&c->QRt, (size_t)N * ne));
   }
   if (ok) A(cudaMallocHost(reinterpret_cast<void**>(&c->host), (2 * ne + 16 + 512) * sizeof(double)));
   if (ok) A(cudaEventCreate(&c->ev0));

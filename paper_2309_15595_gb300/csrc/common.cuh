@@ -121,6 +121,12 @@ cudaError_t max_dev_identity(cudaStream_t s, int64_t n, const double2* U, int64_
                              double* out);
 // M = I, or M -= I with subtract (n x n, ld ldm).
 cudaError_t set_identity(cudaStream_t s, int64_t n, double2* M, int64_t ldm, bool subtract);
+// *out (device) = max over columns j of max_i |R_ij| / max_i |X_ij| (m x n
+// blocks, |z| = max(|Re z|, |Im z|); a zero column of X counts 0 or +inf).
+cudaError_t max_col_ratio(cudaStream_t s, int64_t m, int64_t n, const double2* R, int64_t ldr,
+                          const double2* X, int64_t ldx, double* out);
+// Strict lower triangle of the n x n M (ld ldm) set to zero.
+cudaError_t zero_lower(cudaStream_t s, int64_t n, double2* M, int64_t ldm);
 // G_ii += shift * trace(G) (device scalars only); used for the shifted pass.
 cudaError_t add_trace_shift(cudaStream_t s, int64_t n, double2* G, int64_t ldg, double factor,
                             double* scratch);
@@ -171,10 +177,11 @@ struct JacobiWork {
   int* cl_idx = nullptr;  // clustered column indices, grouped by cluster (n ints)
   int* cl_off = nullptr;  // cluster offsets into cl_idx (n + 1 ints)
   // optional product for the FP64 refinement: P = op(X) B (op(X) = X, M x K, or
-  // X^H for X of K x M), epilogue as for zgemm_nn; null: CUDA-core FP64 products
+  // X^H for X of K x M), epilogue as for zgemm_nn; extended: the accurate
+  // variant for products that cancel; null: CUDA-core FP64 products
   cudaError_t (*gemm)(void* ctx, int64_t M, int64_t K, const double2* X, int64_t ldx,
                       bool conj_trans, int64_t ncols, const double2* B, int64_t ldb,
-                      const Epilogue& ep) = nullptr;
+                      const Epilogue& ep, bool extended) = nullptr;
   void* gemm_ctx = nullptr;
 };
 size_t jacobi_params_elems(int64_t n);

@@ -32,6 +32,7 @@ struct chase_ctx {
   chase::OzakiWork ow{};
   chase::HouseholderWork hw{};  // Householder QR fallback of Alg. 4
   double* oz_partial = nullptr;  // residual partials of the tensor-core path (32-row tiles)
+  double2* QRt = nullptr;        // N x ne: iterate of the tensor-core triangular solve
   bool oz_a_valid = false;       // digits of the current solve's A are prepared
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double2* gw = nullptr;         // gradient workspace (grown on first use)

@@ -261,26 +261,63 @@ __global__ void trace_shift_kernel(int64_t n, double2* G, int64_t ldg, double fa
   for (int64_t i = t; i < n; i += 256) G[i + i * ldg].x += shift;
 }
 
-// max over the upper triangle of |U_ij - delta_ij| (one CTA, fixed order)
-__global__ void __launch_bounds__(1024)
+// Largest of non-negative doubles (NaN counted as +inf) into *out, which holds
+// the bit pattern of a non-negative double (monotone in unsigned order): the
+// result does not depend on the order of the atomics.
+__device__ __forceinline__ void atomic_max_nonneg(double* out, double v) {
+  if (!(v <= 1.7976931348623157e308)) v = __longlong_as_double(0x7ff0000000000000ll);
+  atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double block_max256(double m, double* red) {
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// max over the upper triangle of |U_ij - delta_ij|: one CTA per column
+__global__ void __launch_bounds__(256)
     dev_identity_kernel(int64_t n, const double2* __restrict__ U, int64_t ldu,
                         double* __restrict__ out) {
-  __shared__ double red[1024];
+  __shared__ double red[256];
+  const int64_t j = blockIdx.x;
   double m = 0.0;
-  for (int64_t e = threadIdx.x; e < n * n; e += 1024) {
-    const int64_t i = e % n, j = e / n;
-    if (i > j) continue;
+  for (int64_t i = threadIdx.x; i <= j; i += 256) {
     double2 u = U[i + j * ldu];
     if (i == j) u.x -= 1.0;
     m = fmax(m, sqrt(u.x * u.x + u.y * u.y));
   }
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int w = 512; w >= 1; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
+  m = block_max256(m, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+}
+
+// max_j (max_i |R_ij|) / (max_i |X_ij|), |z| = max(|Re z|, |Im z|): one CTA per column
+__global__ void __launch_bounds__(256)
+    col_ratio_kernel(int64_t m, const double2* __restrict__ R, int64_t ldr,
+                     const double2* __restrict__ X, int64_t ldx, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int64_t j = blockIdx.x;
+  double mr = 0.0, mx = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += 256) {
+    const double2 r = R[i + j * ldr], x = X[i + j * ldx];
+    mr = fmax(mr, fmax(fabs(r.x), fabs(r.y)));
+    mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
   }
-  if (threadIdx.x == 0) out[0] = red[0];
+  mr = block_max256(mr, red);
+  __syncthreads();
+  mx = block_max256(mx, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(out, mx > 0.0 ? mr / mx : (mr > 0.0 ? __longlong_as_double(0x7ff0000000000000ll) : 0.0));
+}
+
+// strict lower triangle of the n x n M set to zero
+__global__ void zero_lower_kernel(int64_t n, double2* __restrict__ M, int64_t ldm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i < n && i > j) M[i + j * ldm] = make_double2(0.0, 0.0);
 }
 
 // M = I (set) or M -= I (subtract), n x n, ld ldm
@@ -391,7 +428,25 @@ cudaError_t triangular_inverse(cudaStream_t s, int64_t n, const double2* U, int6
 
 cudaError_t max_dev_identity(cudaStream_t s, int64_t n, const double2* U, int64_t ldu,
                              double* out) {
-  dev_identity_kernel<<<1, 1024, 0, s>>>(n, U, ldu, out); count_launch();
+  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  dev_identity_kernel<<<(unsigned)n, 256, 0, s>>>(n, U, ldu, out); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t max_col_ratio(cudaStream_t s, int64_t m, int64_t n, const double2* R, int64_t ldr,
+                          const double2* X, int64_t ldx, double* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess || m <= 0 || n <= 0) return e;
+  col_ratio_kernel<<<(unsigned)n, 256, 0, s>>>(m, R, ldr, X, ldx, out); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t zero_lower(cudaStream_t s, int64_t n, double2* M, int64_t ldm) {
+  if (n <= 1) return cudaSuccess;
+  zero_lower_kernel<<<dim3((unsigned)cdiv(n, 128), (unsigned)n, 1), 128, 0, s>>>(n, M, ldm);
+  count_launch();
   return cudaGetLastError();
 }
 

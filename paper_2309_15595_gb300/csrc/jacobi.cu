@@ -1127,18 +1127,18 @@ namespace {
 // refinement products: P = A B (n x n) or P = X^H Y, on the tensor cores when
 // the context supplied a product, else with the CUDA-core kernels
 cudaError_t heev_nn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, const double2* A,
-                    int64_t lda, const double2* B, const Epilogue& ep) {
-  if (tc && wk.gemm) return wk.gemm(wk.gemm_ctx, n, n, A, lda, false, n, B, n, ep);
+                    int64_t lda, const double2* B, const Epilogue& ep, bool extended = false) {
+  if (tc && wk.gemm) return wk.gemm(wk.gemm_ctx, n, n, A, lda, false, n, B, n, ep, extended);
   return zgemm_nn(s, n, n, n, A, lda, B, n, ep);
 }
 cudaError_t heev_cn(cudaStream_t s, const JacobiWork& wk, bool tc, int64_t n, const double2* X,
-                    const double2* Y, double2* P, bool hermitian) {
+                    const double2* Y, double2* P, bool hermitian, bool extended = false) {
   if (tc && wk.gemm) {
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = P;
     ep.ldy = n;
-    cudaError_t e = wk.gemm(wk.gemm_ctx, n, n, X, n, true, n, Y, n, ep);
+    cudaError_t e = wk.gemm(wk.gemm_ctx, n, n, X, n, true, n, Y, n, ep, extended);
     if (e != cudaSuccess || !hermitian) return e;
     return hermitian_part(s, n, P, n);
   }
@@ -1345,21 +1345,26 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
   const double gscale = wk.host_red[0] * std::sqrt((double)n);
   int refine = 0;
   double emax = 1.0, cmax = 0.0;
-  // The digit-sliced tensor-core products (when the context supplies them) carry
-  // an error of about sqrt(n) 2^-47 of ||G||, far above what the Ritz values
-  // need: they serve the first, coarse steps only; once the corrections fall
-  // below 1e-6 the products are the CUDA-core FP64 ones, and so are the final
-  // step and the orthogonalisation.
-  bool tc = wk.gemm != nullptr;
+  // With the digit-sliced tensor-core products (when the context supplies them)
+  // the first, coarse steps use the 21-pair products, whose error (about
+  // sqrt(n) 2^-50 of max|G_i.| max|X_.j| per entry) is far above what the Ritz
+  // values need. Once the corrections fall below 1e-6 the steps are fine ones:
+  // G X, X^H (G X) and X^H X, whose off-diagonal parts cancel to the size of
+  // the corrections, keep the level-8 digit pairs too (error near the digit
+  // rounding of the operands, a few 2^-48 of ||G||, like the CUDA-core FP64
+  // products' sqrt(n) 2^-53), and so does the final orthogonalisation. Without
+  // them, all products are the CUDA-core FP64 ones.
+  const bool tc = wk.gemm != nullptr;
+  bool fine = false;
   const int max_refine = cap(8);
   for (; refine < max_refine; ++refine) {  // 2-4 steps from FP32 accuracy; a slow start gets more
     Epilogue ep{};
     ep.mode = EPI_STORE;
     ep.Y = wk.T;
     ep.ldy = n;
-    if (heev_nn(s, wk, tc, n, G, ldg, X, ep) != cudaSuccess ||         // T = G X
-        heev_cn(s, wk, tc, n, X, wk.T, wk.Gw, false) != cudaSuccess ||   // S = X^H T
-        heev_cn(s, wk, tc, n, X, X, wk.Gw2, true) != cudaSuccess)        // X^H X
+    if (heev_nn(s, wk, tc, n, G, ldg, X, ep, fine) != cudaSuccess ||         // T = G X
+        heev_cn(s, wk, tc, n, X, wk.T, wk.Gw, false, fine) != cudaSuccess ||   // S = X^H T
+        heev_cn(s, wk, tc, n, X, X, wk.Gw2, true, fine) != cudaSuccess)        // X^H X
       return CHASE_CUDA_FAIL();
     oa_lambda_kernel<<<(unsigned)cdiv(n, 128), 128, 0, s>>>(n, wk.Gw, wk.Gw2, lam); count_launch();
     // E into T (T is free once S is formed)
@@ -1391,17 +1396,17 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     emax = wk.host_red[0];
     cmax = wk.host_red[1];
     // the applied correction was ~emax; the error left is ~emax^2 (plus the
-    // products' own error, hence the last step on the CUDA cores)
-    if (emax <= 1e-8 && !tc) {
+    // products' own error, hence the last step with the accurate products)
+    if (emax <= 1e-8 && (!tc || fine)) {
       ++refine;
       break;
     }
-    if (emax <= 1e-6) tc = false;
+    if (emax <= 1e-6) fine = true;
   }
   {
     // the corrections of close pairs carry rounding of order u / gap; one more
     // orthogonalisation step brings X^H X back to I at working precision
-    if (heev_cn(s, wk, false, n, X, X, wk.Gw2, true) != cudaSuccess) return CHASE_CUDA_FAIL();
+    if (heev_cn(s, wk, tc, n, X, X, wk.Gw2, true, true) != cudaSuccess) return CHASE_CUDA_FAIL();
     half_residual_kernel<<<g2, 128, 0, s>>>(n, wk.Gw2, wk.T); count_launch();
     if (cudaMemcpyAsync(Xn, X, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
@@ -1415,11 +1420,11 @@ int jacobi_heev(cudaStream_t s, int64_t n, const double2* G, int64_t ldg, double
     eo.ldx = n;
     eo.Y = Xn;
     eo.ldy = n;
-    if (heev_nn(s, wk, false, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_CUDA_FAIL();
+    if (heev_nn(s, wk, tc, n, X, n, wk.T, eo) != cudaSuccess) return CHASE_CUDA_FAIL();
     std::swap(X, Xn);
   }
   int sw64 = 0;
-  bool conv = emax <= 1e-8 && !tc;
+  bool conv = emax <= 1e-8 && (!tc || fine);
   double2* Zfinal = X;
   double* wsrc = lam;
   bool clustered = false;

@@ -22,13 +22,20 @@
 // below 2^-56 of the leading level).
 // The result is W = 2^(e_i + f_j) (acc 2^-40 + acc67 2^-48), accurate to a few
 // units of 2^-48 relative to |A_i.| |Y_.j| per term: FP64-class.
+// Extended variant (LMAX = 8): the five pairs of level 8 are kept too (26 MMAs
+// per K step instead of 21, level 8 drained into the FP32 accumulator at weight
+// 2^-64). The dropped pairs then weigh at most 2^-58 instead of 2^-50 of
+// 2^(e_i + f_j) per term, so a product over K terms whose result cancels
+// almost completely (a Gram of nearly orthonormal columns with entries near 1,
+// the residual X - T U of a triangular solve) keeps an error near the digit
+// rounding of its operands instead of sqrt(K) 2^-50 of the scales.
 //
 // Kernel structure (128 x 64 real output tile = 32 complex columns, 10 warps):
 //   warp 0    TMA producer: 6 A digit tiles (128 x 32) and 6 B digit tiles
 //             (64 x 32) per K block into a 3-stage ring (64B swizzle)
-//   warp 1    TMEM allocator and MMA issuer: 21 tcgen05.mma (M=128, N=64,
-//             K=16) per 16-wide K step, one accumulator per level (6 x 64
-//             TMEM columns); after each 256-wide chunk it hands the
+//   warp 1    TMEM allocator and MMA issuer: 21 (26) tcgen05.mma (M=128,
+//             N=64, K=16) per 16-wide K step, one accumulator per level (6 (7)
+//             x 64 TMEM columns); after each 256-wide chunk it hands the
 //             accumulators to the epilogue and waits until they are drained
 //   warps 2-9 epilogue: warp w owns TMEM lane quarter w % 4 and half of the
 //             complex columns; int64/FP32 accumulators in registers; at the
@@ -38,6 +45,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 
 #include "ozaki.cuh"
@@ -176,6 +184,7 @@ struct Params {
 };
 
 // ---------------------------------------------------------------- kernel
+template <int LMAX>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       Params P) {
@@ -269,13 +278,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int kk = 0; kk < TK / 16; ++kk) {
             const uint32_t off = kk * 32;
 #pragma unroll
-            for (int L = 2; L <= OS + 1; ++L) {
+            for (int L = 2; L <= LMAX; ++L) {
+              const int sa0 = L - OS > 1 ? L - OS : 1;  // first pair of level L
 #pragma unroll
-              for (int sa = 1; sa < L; ++sa) {
+              for (int sa = sa0; sa < L && sa <= OS; ++sa) {
                 const int tb = L - sa;
                 // every level restarts each 256-long chunk (levels 2-5 then stay
                 // exact integers below 2^24)
-                const uint32_t acc = (kc == 0 && kk == 0 && sa == 1) ? 0u : 1u;
+                const uint32_t acc = (kc == 0 && kk == 0 && sa == sa0) ? 0u : 1u;
                 umma_bf16(tmem + (uint32_t)((L - 2) * TN),
                           sdesc_sw64(st + (sa - 1) * A_TILE + off),
                           sdesc_sw64(st + OS * A_TILE + (tb - 1) * B_TILE + off), acc);
@@ -298,11 +308,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t row = m0 + q * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
     long long acc[2 * HC];                    // re[0..16), im[16..32): levels 2-5, weight 2^-40
-    float acc67[2 * HC];                      // levels 6-7, weight 2^-48
+    // levels 6-LMAX, weight 2^-48. In the extended variant they are summed over
+    // the chunks in FP64: its products are Grams whose diagonal adds squared
+    // digits coherently (sum_k d_3(x_k)^2 grows like K), where FP32 sums over
+    // K = 80000 lost about 2^-44 of the scale (orthogonality 2e-11 at
+    // N = 40000 after CholeskyQR2); per chunk the values stay below 2^25.
+    using Acc67 = typename std::conditional<LMAX == 8, double, float>::type;
+    Acc67 acc67[2 * HC];
 #pragma unroll
     for (int j = 0; j < 2 * HC; ++j) {
       acc[j] = 0;
-      acc67[j] = 0.f;
+      acc67[j] = Acc67(0);
     }
     bool go = true;
     for (int c = 0; c < nchunks; ++c) {
@@ -320,25 +336,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int part = 0; part < 2; ++part) {  // real columns, then imaginary
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {         // levels 2-3, 4-5, 6-7
+        for (int g = 0; g < LMAX / 2; ++g) {  // levels 2-3, 4-5, 6-7 (, 8)
           float v[2][HC];
 #pragma unroll
           for (int l = 0; l < 2; ++l)
-            tmem_ld16(tl + (uint32_t)((2 * g + l) * TN + part * CT + h * HC), v[l]);
+            if (2 + 2 * g + l <= LMAX)
+              tmem_ld16(tl + (uint32_t)((2 * g + l) * TN + part * CT + h * HC), v[l]);
           tmem_wait_ld();
 #pragma unroll
           for (int l = 0; l < 2; ++l) {
             const int L = 2 + 2 * g + l;
+            if (L > LMAX) continue;
             if (L <= 5) {
               const int sh = 8 * (5 - L);
 #pragma unroll
               for (int j = 0; j < HC; ++j)
                 acc[part * HC + j] += (long long)__float2int_rn(v[l][j]) << sh;
             } else {
-              const float w = L == 6 ? 1.0f : 0.00390625f;
+              const Acc67 w = L == 6 ? Acc67(1) : (L == 7 ? Acc67(0x1p-8) : Acc67(0x1p-16));
 #pragma unroll
               for (int j = 0; j < HC; ++j)
-                acc67[part * HC + j] = fmaf(w, v[l][j], acc67[part * HC + j]);
+                acc67[part * HC + j] = fma(w, (Acc67)v[l][j], acc67[part * HC + j]);
             }
           }
         }
@@ -489,6 +507,27 @@ __global__ void slice_a_kernel(int64_t M, int64_t K, int64_t Np, bool skip_diag,
   }
 }
 
+// X (M x K, column-major) <- the value its six digits represent when X is the
+// left operand (row i scaled by 2^-e_i): sum_s d_s 2^(e_i - 8s).
+__global__ void round_left_kernel(int64_t M, int64_t K, double2* __restrict__ X, int64_t ldx,
+                                  const int* __restrict__ ea) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t k = blockIdx.y;
+  if (i >= M || k >= K) return;
+  const double2 x = X[i + k * ldx];
+  const double s = ldexp(1.0, -ea[i]);
+  __nv_bfloat16 dr[OS], di[OS];
+  digits_of(x.x * s, dr);
+  digits_of(x.y * s, di);
+  double vr = 0.0, vi = 0.0;
+#pragma unroll
+  for (int d = OS - 1; d >= 0; --d) {  // exact: 48 bits below the scale
+    vr = (vr + __bfloat162float(dr[d])) * (1.0 / 256.0);
+    vi = (vi + __bfloat162float(di[d])) * (1.0 / 256.0);
+  }
+  X[i + k * ldx] = make_double2(ldexp(vr, ea[i]), ldexp(vi, ea[i]));
+}
+
 // Left operand X^H for X (K x M, column-major): row i of X^H is conj(X[:, i]),
 // contiguous, so no transpose is needed. Exponents per row come from colexp.
 __global__ void slice_ct_kernel(int64_t M, int64_t K, int64_t Np, const double2* __restrict__ X,
@@ -623,7 +662,10 @@ cudaError_t ozaki_alloc(OzakiWork& w, int64_t N, int64_t ne) {
   if (!make_map(&maps->a, w.Ad, (int64_t)OS * N, w.Np, TM) ||
       !make_map(&maps->b, w.Bd, (int64_t)OS * w.brows, w.Np, TN))
     return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(ozaki_gemm_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(ozaki_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               SMEM_BYTES);
 }
 
@@ -689,14 +731,14 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
   P.partial = ep.partial;
   P.err = w.err;
   const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / CT - j0 / CT + 1), 1);
-  ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
+  ozaki_gemm_kernel<7><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const double2* X,
                                int64_t ldx, bool conj_trans, int64_t ncols, const double2* B,
-                               int64_t ldb, const Epilogue& ep, OzakiWork& w) {
+                               int64_t ldb, const Epilogue& ep, OzakiWork& w, bool extended) {
   if (M <= 0 || ncols <= 0 || K <= 0) return cudaSuccess;
   const int64_t Kp = ozaki_np(K);
   if (Kp > w.Np || ncols > w.ne || (size_t)OS * M * 2 * Kp > w.l_elems)
@@ -762,7 +804,27 @@ cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const doubl
   P.partial = ep.partial;
   P.err = w.err;
   const dim3 grid((unsigned)cdiv(M, TM), (unsigned)((ncols - 1) / CT + 1), 1);
-  ozaki_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, P);
+  if (extended)
+    ozaki_gemm_kernel<8><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, P);
+  else
+    ozaki_gemm_kernel<7><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, P);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_round_left(cudaStream_t s, int64_t M, int64_t K, double2* X, int64_t ldx,
+                             OzakiWork& w) {
+  if (M <= 0 || K <= 0) return cudaSuccess;
+  if (M > w.N) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(w.amax, 0, M * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  rowmax_kernel<<<dim3((unsigned)cdiv(M, 256), (unsigned)cdiv(K, 256), 1), 256, 0, s>>>(
+      M, K, false, X, ldx, w.amax);
+  count_launch();
+  exps_kernel<<<(unsigned)cdiv(M, 256), 256, 0, s>>>(M, w.amax, w.el);
+  count_launch();
+  round_left_kernel<<<dim3((unsigned)cdiv(M, 256), (unsigned)K, 1), 256, 0, s>>>(M, K, X, ldx,
+                                                                                 w.el);
   count_launch();
   return cudaGetLastError();
 }

@@ -36,9 +36,20 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
 // P = op(X) * B for the N x n^2 products: op(X) = X (M x K, column-major) or,
 // with conj_trans, X^H for X of K x M; B is K x ncols. No diagonal split. The
 // epilogue uses absolute columns 0 .. ncols of B, X, Y. K <= N, ncols <= ne.
+// extended: also keep the digit pairs of level 8 (26 instead of 21 products;
+// the dropped pairs weigh 2^-58 instead of 2^-50 of the row and column scales),
+// for products whose result cancels almost completely.
 cudaError_t ozaki_gemm_general(cudaStream_t s, int64_t M, int64_t K, const double2* X,
                                int64_t ldx, bool conj_trans, int64_t ncols, const double2* B,
-                               int64_t ldb, const Epilogue& ep, OzakiWork& w);
+                               int64_t ldb, const Epilogue& ep, OzakiWork& w,
+                               bool extended = false);
+// X (M x K, column-major, M <= N) <- the digits it has as the left
+// operand of ozaki_gemm_general (rows scaled by powers of two, six digits), so
+// that such a product takes X exactly: a change of at most 2^-49 of each row's
+// scale, leaving the row maxima (and so the scales) as they were except when a
+// maximum rounds up to the next power of two.
+cudaError_t ozaki_round_left(cudaStream_t s, int64_t M, int64_t K, double2* X, int64_t ldx,
+                             OzakiWork& w);
 // *out (device) = the largest row exponent e of the last general product's left
 // operand (rows scaled by 2^-e to |x| < 1/2): bounds its digit-sliced error.
 cudaError_t ozaki_left_exp_max(cudaStream_t s, int64_t M, OzakiWork& w, int* out);

@@ -135,3 +135,58 @@ def test_tensor_fp64_solve_c1(lib, precision):
     res = np.linalg.norm(A @ V - V * r[None, :], axis=0)
     assert res.max() <= 1e-10 * nA
     assert np.abs(V.conj().T @ V - np.eye(p.nev)).max() <= 1e-12
+
+
+def localized_orthonormal(m, n, seed):
+    """Orthonormal columns that each hold one entry near 1 (a nearly converged
+    block of localised eigenvectors): the digit scale of every column is the
+    largest possible, which is the worst case for the digit-sliced products."""
+    rng = np.random.default_rng(seed)
+    E = np.zeros((m, n), dtype=np.complex128)
+    E[rng.permutation(m)[:n], np.arange(n)] = 1.0
+    Z = complex_normal(seed, 96, m * n).reshape(n, m).T
+    Q, R = np.linalg.qr(E + 0.02 * Z)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))[None, :]
+
+
+@pytest.mark.parametrize("m,n,kappa,kind", [
+    (2037, 200, 1e3, "collinear"), (2037, 200, 1e6, "collinear"), (700, 130, 1e5, "graded"),
+    (2037, 200, 1e7, "graded"), (1500, 300, 3e7, "collinear")])
+@pytest.mark.parametrize("tensor", [0, 1])
+def test_qr_triangular_solve_is_backward_stable(lib, m, n, kappa, kind, tensor):
+    """X = Q0 T with Q0 localised and orthonormal and T upper triangular with a
+    positive diagonal, so Q0 is the exact Q factor. kind = collinear: T =
+    diag(s) (I + U) (every column dominated by the first: a filtered block's
+    true ill-conditioning, kappa(X) ~ kappa); graded: T = (I + U) diag(s)
+    (columns scaled over kappa: equilibrated, X is well conditioned).
+
+    The span test holds at any kappa: with P the orthogonal projector onto
+    span(Q) (from an exactly orthonormalised copy of Q, so that Q's own
+    orthogonality error does not enter), a QR whose span is that of X + dX
+    gives ||X_j - P X_j|| <= ||dX_j|| for every column, and the bound
+    2e-14 ||X_j|| is the backward error the triangular solves may leave (the
+    oracle's FP64 CholeskyQR2 gives about 1e-15 here, LAPACK's Householder QR
+    the same). The forward error ||Q - Q0|| is that backward error times the
+    conditioning of the columns' directions: at most 1e-12 for the graded
+    block, and 2e-15 kappa for the collinear one (the oracle's FP64
+    CholeskyQR2 gives |Q - Q0| of about 6e-18 kappa on the collinear ones)."""
+    Q0 = localized_orthonormal(m, n, int(kappa) % 1000 + n)
+    s = np.logspace(0, -np.log10(kappa), n)
+    U = np.triu(complex_normal(n, 97, n * n).reshape(n, n), 1) * (0.3 / np.sqrt(n))
+    T = (s[:, None] * (np.eye(n) + U)) if kind == "collinear" else ((np.eye(n) + U) * s[None, :])
+    X = np.asfortranarray(Q0 @ T)
+    with lib.Context(lib.default_params(m, n, 0, fp64_tensor=tensor)) as ctx:
+        Xd = dev(X, lib)
+        v = ctx.chase_qr(Xd, n, kappa)
+        Q = Xd.cpu().numpy()
+    orth = np.abs(Q.conj().T @ Q - np.eye(n)).max()
+    P = np.linalg.qr(Q)[0]
+    span = (np.linalg.norm(X - P @ (P.conj().T @ X), axis=0) / np.linalg.norm(X, axis=0)).max()
+    fwd = np.abs(Q - Q0).max()
+    print(f"{kind} m={m} n={n} kappa={kappa:.0e} tensor={tensor}: variant {v}, orth {orth:.2e}, "
+          f"span residual {span:.2e}, |Q - Q0| {fwd:.2e}")
+    assert orth <= 1e-12
+    assert span <= 2e-14
+    assert fwd <= (1e-12 if kind == "graded" else 2e-15 * kappa)
+    R = Q.conj().T @ X
+    assert np.all(np.diag(R).real > 0)
