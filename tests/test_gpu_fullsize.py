@@ -193,3 +193,32 @@ def test_solve_clustered_uses_cluster_finish(lib):
     assert np.abs(got - p.eigenvalues()[:p.nev]).max() <= 1e-10 * nA
     assert (np.linalg.norm(A @ V - V * got[None, :], axis=0) / nA).max() <= 1e-10
     assert np.abs(V.conj().T @ V - np.eye(p.nev)).max() <= 1e-12
+
+
+def test_qr_localized_block_at_k80000(lib):
+    """CholeskyQR2 with the tensor-core products of X = Q0 T at N = 40000
+    (K = 80000 in the Grams), Q0 orthonormal with one entry near 1 per column.
+    The Grams' diagonals add squared digits coherently over K; summed across the
+    256-long chunks in FP32 they were off by about 2^-44 of the scale at this K,
+    which left orthogonality near 1e-12 here (2e-11 in the C3 solve); with the
+    FP64 sums it stays at the digit rounding, a few 1e-14."""
+    N, n = 40000, 128
+    rng = np.random.default_rng(40)
+    E = np.zeros((N, n), dtype=np.complex128)
+    E[rng.permutation(N)[:n], np.arange(n)] = 1.0
+    Z = complex_normal(40, 98, N * n).reshape(n, N).T
+    Q0, R0 = np.linalg.qr(E + 0.02 * Z)
+    Q0 = Q0 * (np.diag(R0) / np.abs(np.diag(R0)))[None, :]
+    T = np.eye(n) + np.triu(complex_normal(41, 99, n * n).reshape(n, n), 1) * (0.3 / np.sqrt(n))
+    X = np.asfortranarray(Q0 @ T)
+    with lib.Context(lib.default_params(N, n, 0, fp64_tensor=1)) as ctx:
+        Xd = lib.colmajor(torch.from_numpy(X).cuda())
+        v = ctx.chase_qr(Xd, n, 100.0)
+        G = (Xd.mH @ Xd).cpu().numpy()
+        Q = Xd.cpu().numpy()
+    orth = np.abs(G - np.eye(n)).max()
+    fwd = np.abs(Q - Q0).max()
+    print(f"localized QR N={N} n={n}: variant {v}, orth {orth:.2e}, |Q - Q0| {fwd:.2e}")
+    assert v == lib.CHASE_QR_CHOLQR2
+    assert orth <= 1e-13
+    assert fwd <= 1e-12
