@@ -654,11 +654,16 @@ __global__ void __launch_bounds__(BJ_T)
   float2 (*S)[BJ_M + 1] = reinterpret_cast<float2 (*)[BJ_M + 1]>(bj_smem);
   float2 (*R)[BJ_M + 1] = reinterpret_cast<float2 (*)[BJ_M + 1]>(bj_smem + BJ_M * (BJ_M + 1));
   __shared__ RotT<float> rots[BJ_M / 2];
+  __shared__ int pq[BJ_M / 2][2];  // this round's index pairs
   const int k = blockIdx.x, t = threadIdx.x;
   int64_t i0, j0;
   int ni, nj;
   bj_pair(n, nb, nbp, round, k, i0, ni, j0, nj);
   const int m = ni + nj;
+  // a full pair (m = 64, the common case): thread t always takes row/column
+  // t % 64 of the pairs t / 64, t / 64 + 4, ... (no index arithmetic per element)
+  static_assert(BJ_T % BJ_M == 0, "fixed element mapping");
+  const bool full = m == BJ_M;
   for (int e = t; e < m * m; e += BJ_T) {
     const int a = e % m, c = e / m;
     S[a][c] = G[bj_gidx(a, i0, ni, j0) + bj_gidx(c, i0, ni, j0) * n];
@@ -670,30 +675,51 @@ __global__ void __launch_bounds__(BJ_T)
     if (t < mp / 2) {
       int p, q;
       rr_pair(mp, rd, t, p, q);
+      pq[t][0] = p;
+      pq[t][1] = q;
       rots[t] = q < m ? make_rot_t<float>(S[p][p].x, S[q][q].x, S[p][q])
                       : make_rot_t<float>(0.f, 0.f, make_float2(0.f, 0.f));
     }
     __syncthreads();
-    for (int e = t; e < (mp / 2) * m; e += BJ_T) {  // column rotations of S and R
-      const int kk = e / m, i = e % m;
-      int p, q;
-      rr_pair(mp, rd, kk, p, q);
-      if (q >= m || rots[kk].s == 0.f) continue;
-      rot_cols_t(S[i][p], S[i][q], rots[kk]);
-      rot_cols_t(R[i][p], R[i][q], rots[kk]);
+    if (full) {  // column rotations of S and R
+      const int i = t % BJ_M;
+#pragma unroll 4
+      for (int kk = t / BJ_M; kk < BJ_M / 2; kk += BJ_T / BJ_M) {
+        const RotT<float> r = rots[kk];
+        if (r.s == 0.f) continue;
+        const int p = pq[kk][0], q = pq[kk][1];
+        rot_cols_t(S[i][p], S[i][q], r);
+        rot_cols_t(R[i][p], R[i][q], r);
+      }
+    } else {
+      for (int e = t; e < (mp / 2) * m; e += BJ_T) {
+        const int kk = e / m, i = e % m;
+        const int p = pq[kk][0], q = pq[kk][1];
+        if (q >= m || rots[kk].s == 0.f) continue;
+        rot_cols_t(S[i][p], S[i][q], rots[kk]);
+        rot_cols_t(R[i][p], R[i][q], rots[kk]);
+      }
     }
     __syncthreads();
-    for (int e = t; e < (mp / 2) * m; e += BJ_T) {  // row rotations of S
-      const int kk = e / m, j = e % m;
-      int p, q;
-      rr_pair(mp, rd, kk, p, q);
-      if (q >= m || rots[kk].s == 0.f) continue;
-      rot_rows_t(S[p][j], S[q][j], rots[kk]);
+    if (full) {  // row rotations of S
+      const int j = t % BJ_M;
+#pragma unroll 4
+      for (int kk = t / BJ_M; kk < BJ_M / 2; kk += BJ_T / BJ_M) {
+        const RotT<float> r = rots[kk];
+        if (r.s == 0.f) continue;
+        rot_rows_t(S[pq[kk][0]][j], S[pq[kk][1]][j], r);
+      }
+    } else {
+      for (int e = t; e < (mp / 2) * m; e += BJ_T) {
+        const int kk = e / m, j = e % m;
+        const int p = pq[kk][0], q = pq[kk][1];
+        if (q >= m || rots[kk].s == 0.f) continue;
+        rot_rows_t(S[p][j], S[q][j], rots[kk]);
+      }
     }
     __syncthreads();
     if (t < mp / 2) {  // the rotated 2 x 2 block exactly
-      int p, q;
-      rr_pair(mp, rd, t, p, q);
+      const int p = pq[t][0], q = pq[t][1];
       if (q < m && rots[t].s != 0.f) {
         S[p][p] = make_float2(rots[t].app, 0.f);
         S[q][q] = make_float2(rots[t].aqq, 0.f);
