@@ -52,7 +52,13 @@ OZ_PAIRS = 21.0
 # DRAM bytes (read + write) of one filter launch at full size, from ncu captures of the
 # current kernels (see profiles/), keyed by (kernel, N, nev + nex). Empty entries: the
 # kernel changed after the last capture.
-FILTER_DRAM_BYTES = {}
+FILTER_DRAM_BYTES = {
+    # one-pass capture of a timed-step launch at C3 (profiles/mixed_filter_C3_traffic.md):
+    # 204.48 GB read + 2.88 GB written, against 19.5 GB algorithmic (A's hi/lo BF16 planes
+    # 12.8 GB, the operand planes read and the next ones written 3.8 GB, three FP32 states
+    # of the 3000 columns 2.9 GB)
+    ("mixed", 40000, 3000): 207.36e9,
+}
 # FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
