@@ -20,9 +20,11 @@ job (N replicas for --gpus N; a single solve does not shard).
 The same JSON line carries, when the wall-clock budget allows (single GPU
 only), one time-to-solution solve (resid <= 1e-10 ||A||) in the mixed mode and
 one in the plain FP64 mode on the same code, each checked against the exactly
-known spectrum and by recomputing sampled residuals with torch. Legs that do
-not fit the budget are skipped and named in the line; the line is always
-printed (also on SIGTERM).
+known spectrum and by recomputing sampled residuals with torch, and two further
+workloads: the batched warm-start sequence (C5, 96 problems x 10 steps, solves/s)
+and the differentiation workload (C4, forward/backward times and a central
+finite-difference check of the gradient). Legs that do not fit the budget are
+skipped and named in the line; the line is always printed (also on SIGTERM).
 
 ``--impl reference`` times the CPU FP64 oracle on a bounded sample of the same
 workload instead.
@@ -111,6 +113,10 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=96)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-threads", type=int, default=8)
+    ap.add_argument("--legs", default="batch,grad",
+                    help="further workloads carried in the headline line (single GPU, within "
+                         "the budget): batch = the C5 warm-start sequence, grad = the C4 "
+                         "gradient timing and finite-difference check; empty to skip")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -626,6 +632,34 @@ def run_gpu(args):
             "roofline": filter_roofline(lib, vprec, vt, vfilter, N, ne, deg),
             "phase_ms": {k: sum(x[k] for x in vstats) / len(vstats) for k in PHASES},
             "gpu_launches": int(sum(x["kernel_launches"] for x in vstats))}
+    # the C4 and C5 workloads as legs of the same line (single GPU): the C3 buffers go first
+    extra = [m for m in args.legs.split(",") if m] if world == 1 else []
+    if extra:
+        del Ad, V0d, Q0d, V, ritz, resid
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    for leg in extra:
+        est = {"batch": 150.0, "grad": 90.0}.get(leg)
+        if est is None:
+            out.d.setdefault("errors", []).append(f"unknown leg {leg}")
+            continue
+        if elapsed() + est > args.budget_s:
+            out.d["skipped"].append(f"{leg}: estimated {est:.0f} s exceeds the budget")
+            continue
+        t0 = elapsed()
+        try:
+            if leg == "batch":
+                out.d["batch_c5"] = batch_leg(lib, torch, dev, args.batch_problems,
+                                              args.batch_steps, args.batch_threads,
+                                              args.fp64_tensor)
+                out.d["batch_c5"]["wall_s"] = elapsed() - t0
+            else:
+                out.d["grad_c4"] = grad_leg(lib, torch, dev, 3, 1, args.grad_fd,
+                                            args.fp64_tensor)
+                out.d["grad_c4"]["wall_s"] = elapsed() - t0
+        except Exception as exc:  # an optional leg never costs the line
+            out.d.setdefault("errors", []).append(f"{leg}: {exc}")
+            torch.cuda.empty_cache()
     out.d["wall_s"] = elapsed()
     if rank == 0:
         out.emit()
@@ -662,22 +696,28 @@ def run_tts(args):
     return 0
 
 
-def run_grad(args):
+def c4_loss_torch(torch, A, Bt, w, nev):
+    """L = sum_i w_i lambda_i + ||X^H B X||_F^2 of the nev lowest eigenpairs of A,
+    from torch's dense eigendecomposition (cuSOLVER): the finite-difference
+    reference of the gradient check. The loss is invariant under a phase change of
+    any eigenvector, so the eigenvectors' phases do not matter."""
+    lam, X = torch.linalg.eigh(A)
+    X = X[:, :nev]
+    M = X.mH @ Bt @ X
+    return float(torch.dot(w, lam[:nev]) + torch.sum(torch.abs(M) ** 2))
+
+
+def grad_leg(lib, torch, dev, steps, warmup, fd_dirs, fp64_tensor):
     """Differentiation workload (C4: N=4096, nev=64, nex=32, uniform [0, 10] with a
     0.05 gap after index 64): L = sum w_i lambda_i + ||X^H B X||_F^2 through the
     autograd Function over chase_solve / chase_eig_vjp, and the filter adjoint
     (degree 20, checkpoints every 5 steps). Times forward and backward with CUDA
-    events; checks the gradient against the oracle's exact gradient and against
-    central differences (h = 1e-6) along --grad-fd random Hermitian directions."""
-    import torch
-
-    import paper_2309_15595_gb300 as lib
-    from oracle import grad_oracle as G
+    events on the launching stream; checks the gradient against central
+    differences (h = 1e-6) of the loss along ``fd_dirs`` random Hermitian
+    directions, each loss from torch's dense eigendecomposition in FP64."""
     from paper_2309_15595_gb300.autograd import chase_eigh, chebyshev_filter
     from synth import complex_normal, config_problem, uniform01
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     p = config_problem("C4")
     N = p.N
     Ad = p.matrix_torch(dev)
@@ -693,8 +733,7 @@ def run_grad(args):
         At = Ad.clone().requires_grad_(True)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        lam, X, _ = chase_eigh(At, V0, p.nev, p.nex, lanczos_start=Q0,
-                               fp64_tensor=args.fp64_tensor)
+        lam, X, _ = chase_eigh(At, V0, p.nev, p.nex, lanczos_start=Q0, fp64_tensor=fp64_tensor)
         M = X.conj().T @ Bt @ X
         loss = torch.dot(w, lam) + torch.sum(torch.abs(M) ** 2)
         e1.record(stream)
@@ -714,7 +753,7 @@ def run_grad(args):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         Y = chebyshev_filter(At, Vt, 20, c, e, float(lam_all[0]), checkpoint=5,
-                             fp64_tensor=args.fp64_tensor)
+                             fp64_tensor=fp64_tensor)
         loss = torch.real(torch.sum(Wt.conj() * Y))
         e1.record(stream)
         loss.backward()
@@ -722,48 +761,60 @@ def run_grad(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), e1.elapsed_time(e2)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         eig_step()
         filter_step()
-    eig_t = [eig_step() for _ in range(args.steps)]
-    fil_t = [filter_step() for _ in range(args.steps)]
-    Ag = eig_t[-1][0].cpu().numpy()
-    A0 = Ad.cpu().numpy()
-    B = Bt.cpu().numpy()
-    wn = w.cpu().numpy()
-    t0 = time.perf_counter()
-    lam0, X0 = G.lowest_eigenpairs(A0, p.nev)
-    ref = G.eig_vjp(A0, p.nev, wn, G.c4_loss_adjoints(lam0, X0, wn, B)[1])
-    t_oracle = time.perf_counter() - t0
-    rel = float(np.linalg.norm(Ag - ref) / np.linalg.norm(ref))
-    fd_worst = None
-    if args.grad_fd > 0:
+    eig_t = [eig_step() for _ in range(steps)]
+    fil_t = [filter_step() for _ in range(steps)]
+    Ag = eig_t[-1][0]
+    fd_worst, t_fd = None, 0.0
+    if fd_dirs > 0:
+        t0 = time.perf_counter()
         h = 1e-6
-        L0 = G.c4_loss(lam0, X0, wn, B)
+        A0 = Ad.contiguous()
+        L0 = c4_loss_torch(torch, A0, Bt, w, p.nev)
         fd_worst = 0.0
-        for k in range(args.grad_fd):
-            Zk = complex_normal(4, 700 + k, N * N).reshape(N, N)
+        for k in range(fd_dirs):
+            Zk = torch.from_numpy(complex_normal(4, 700 + k, N * N).reshape(N, N)).to(dev)
             E = 0.5 * (Zk + Zk.conj().T)
-            E /= np.abs(np.linalg.eigvalsh(E)).max()
-            Lp = G.c4_loss(*G.lowest_eigenpairs(A0 + h * E, p.nev), wn, B)
-            Lm = G.c4_loss(*G.lowest_eigenpairs(A0 - h * E, p.nev), wn, B)
-            fd = (Lp - Lm) / (2 * h)
-            an = float(np.real(np.sum(Ag.conj() * E)))
+            del Zk
+            E /= torch.linalg.eigvalsh(E).abs().max()
+            fd = (c4_loss_torch(torch, A0 + h * E, Bt, w, p.nev)
+                  - c4_loss_torch(torch, A0 - h * E, Bt, w, p.nev)) / (2 * h)
+            an = float(torch.real(torch.sum(Ag.conj() * E)))
             fd_worst = max(fd_worst, abs(fd - an) / max(abs(an), 1e-3 * abs(L0)))
+            del E
+        t_fd = time.perf_counter() - t0
     med = statistics.median
+    out = {"config": {"workload": "C4: gap spectrum, N=4096, nev=64, nex=32; loss sum w_i "
+                                  "lambda_i + ||X^H B X||_F^2; filter adjoint degree 20, "
+                                  "checkpoint 5, on 96 columns",
+                      "fp64_tensor": fp64_tensor},
+           "steps": steps, "warmup": warmup,
+           "eig_forward_ms": med([t[1] for t in eig_t]),
+           "eig_backward_ms": med([t[2] for t in eig_t]),
+           "filter_forward_ms": med([t[0] for t in fil_t]),
+           "filter_backward_ms": med([t[1] for t in fil_t]),
+           "fd_directions": fd_dirs, "fd_step": 1e-6, "fd_worst_rel_mismatch": fd_worst,
+           "fd_reference": "central differences of the loss from torch.linalg.eigh (FP64)",
+           "fd_s": t_fd,
+           "fd_within_1e-6": (fd_worst is not None and fd_worst <= 1e-6)}
+    del Ad, Bt, V0, Q0, Wt, Ag, eig_t
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_grad(args):
+    """Standalone differentiation workload (C4); see grad_leg."""
+    import torch
+
+    import paper_2309_15595_gb300 as lib
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    res = grad_leg(lib, torch, dev, args.steps, args.warmup, args.grad_fd, args.fp64_tensor)
     line = {"metric": METRIC, "kind": "gradient", "unit": "ms", "higher_is_better": False,
-            "config": {"workload": "C4: gap spectrum, N=4096, nev=64, nex=32; loss sum w_i "
-                                   "lambda_i + ||X^H B X||_F^2; filter adjoint degree 20, "
-                                   "checkpoint 5, on 96 columns",
-                       "fp64_tensor": args.fp64_tensor},
-            "steps": args.steps, "warmup": args.warmup,
-            "eig_forward_ms": med([t[1] for t in eig_t]),
-            "eig_backward_ms": med([t[2] for t in eig_t]),
-            "filter_forward_ms": med([t[0] for t in fil_t]),
-            "filter_backward_ms": med([t[1] for t in fil_t]),
-            "grad_rel_err_vs_oracle": rel, "oracle_gradient_s": t_oracle,
-            "fd_directions": args.grad_fd, "fd_worst_rel_mismatch": fd_worst,
-            "data": "synthetic"}
+            **res, "data": "synthetic"}
     print(json.dumps(line))
     return 0
 
@@ -788,20 +839,116 @@ def batch_sizes(nprob):
     return [int(256 + (4096 - 256) * u) for u in uniform01(5, 1, nprob)]
 
 
+def perturbation(torch, N, dev, seed):
+    """E, a seeded Hermitian Gaussian N x N matrix scaled to ||E||_2 = 1 (the C5
+    sequence's A_{t+1} = A_t + 1e-3 E_t). Drawn on the device by torch's seeded
+    generator: the host generator would take about a minute per step for 96
+    problems. ||E||_2 by 40 power steps on E^2 (input generation, not the method)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    Z = torch.randn(N, N, dtype=torch.complex128, device=dev, generator=g)
+    E = 0.5 * (Z + Z.mH)
+    del Z
+    x = torch.ones(N, 1, dtype=E.dtype, device=dev)
+    for _ in range(40):
+        x = E @ (E @ x)
+        x /= torch.linalg.vector_norm(x)
+    E /= torch.linalg.vector_norm(E @ x)
+    return E
+
+
+def batch_leg(lib, torch, dev, nprob, nsteps, threads, fp64_tensor, rank=0, world=1, dist=None):
+    """Batched warm-start sequence (C5): ``nprob`` problems with N drawn uniformly
+    from [256, 4096], nev = ceil(N/20), nex = ceil(N/40), uniform spectra in
+    [0, 10], 8 reflectors; each solved ``nsteps`` times as
+    A_{t+1} = A_t + 1e-3 E_t (||E_t||_2 = 1), warm-started from the previous Ritz
+    vectors, mixed-precision filter, all problems of a step in one
+    chase_solve_batch call. Perturbations are made outside the timed region; each
+    step's batch call is timed with CUDA events. With several ranks the problems
+    are split over them by cost (N^2 (nev + nex)), with no collective on the data
+    path; the time is the slowest rank's. Checks: the first step's eigenvalues
+    against the exactly known spectra, and the last step's residuals recomputed
+    with torch for all wanted pairs of every problem."""
+    from synth import Problem
+
+    Ns = batch_sizes(nprob)
+    costs = [float(N) ** 2 * (-(-N // 20) - (-N // 40)) for N in Ns]
+    mine = shard_problems(costs, world)[rank]
+    probs = [Problem(N=Ns[k], nev=-(-Ns[k] // 20), nex=-(-Ns[k] // 40), spectrum="uniform",
+                     lo=0.0, hi=10.0, reflectors=8, seed=1000 + k) for k in mine]
+    As = [p.matrix_torch(dev) for p in probs]
+    streams = [torch.cuda.Stream(dev) for _ in probs]
+    ctxs = [lib.Context(lib.default_params(p.N, p.nev, p.nex, precision=lib.CHASE_MIXED_BF16X3,
+                                           fp64_tensor=fp64_tensor), s)
+            for p, s in zip(probs, streams)]
+    Vs = [lib.colmajor(torch.from_numpy(p.start_block()).to(dev)) for p in probs]
+    rz = [torch.zeros(p.ne, dtype=torch.float64, device=dev) for p in probs]
+    rs = [torch.zeros_like(r) for r in rz]
+
+    step_ms, iters, mvs, launches, not_conv = [], [], [], [], 0
+    eig_err = 0.0
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for t in range(nsteps):
+        if t > 0:
+            for k, p, A in zip(mine, probs, As):
+                E = perturbation(torch, p.N, dev, 1_000_003 * (k + 1) + t)
+                A.add_(1e-3 * E)  # elementwise on the logical matrix (A keeps its strides)
+                del E
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats, status = lib.solve_batch(ctxs, As, Vs, rz, rs, threads=threads,
+                                        allow_not_converged=True)
+        for s in streams:
+            torch.cuda.current_stream().wait_stream(s)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(sum(st["iters"] for st in stats))
+        mvs.append(sum(st["matvecs"] for st in stats))
+        launches.append(sum(st["kernel_launches"] for st in stats))
+        not_conv += sum(1 for s in status if s != 0)
+        if t == 0:
+            for p, r in zip(probs, rz):
+                lam = torch.from_numpy(p.eigenvalues()[:p.nev]).to(dev)
+                eig_err = max(eig_err, float((r[:p.nev] - lam).abs().max()) / p.norm2())
+    clk = clocks.stop()
+    res_worst = 0.0
+    for p, A, V, r in zip(probs, As, Vs, rz):
+        X = V[:, :p.nev]
+        R = A @ X - X * r[:p.nev].unsqueeze(0)
+        res_worst = max(res_worst, float(torch.linalg.vector_norm(R, dim=0).max()) / p.norm2())
+    for cx in ctxs:
+        cx.close()
+    del As, Vs, rz, rs, ctxs
+    torch.cuda.empty_cache()
+    # whole job: all problems, the slowest rank's time (no collective on the data path)
+    _, total_ms, world = aggregate_over_ranks(sum(step_ms), 1, dist, dev)
+    total = total_ms / 1000.0
+    return {"value": nprob * nsteps / total, "unit": "solves/s", "higher_is_better": True,
+            "n_gpus": world, "scaling": "strong",
+            "config": {"workload": f"C5: {nprob} problems, N uniform in [256, 4096], nev = "
+                                   f"ceil(N/20), nex = ceil(N/40), {nsteps} steps A += 1e-3 E, "
+                                   "warm starts, mixed filter",
+                       "threads": threads, "fp64_tensor": fp64_tensor,
+                       "parallelism": "problems split over ranks by cost" if world > 1
+                                      else "single GPU"},
+            "total_s": total, "step_ms_rank0": step_ms, "iterations_per_step_rank0": iters,
+            "matvecs_per_step_rank0": mvs, "gpu_launches_per_step_rank0": launches,
+            "not_converged_rank0": not_conv,
+            "max_rel_eig_err_step0_rank0": eig_err,
+            "max_rel_resid_recomputed_last_step_rank0": res_worst,
+            "checks": "step 0 eigenvalues vs the exact spectra; last step residuals of all "
+                      "wanted pairs recomputed with torch, relative to ||A_0||_2",
+            "clocks": clk}
+
+
 def run_batch(args):
-    """Batched warm-start sequence (C5): --batch-problems problems with N drawn
-    uniformly from [256, 4096], nev = ceil(N/20), nex = ceil(N/40), uniform
-    spectra, 8 reflectors; each solved --batch-steps times as
-    A_{t+1} = A_t + 1e-3 E_t (||E_t||_2 = 1), warm-started from the previous
-    Ritz vectors, mixed-precision filter, all problems of a step in one
-    chase_solve_batch call. Perturbations are generated outside the timed
-    region; each step's batch call is timed with CUDA events. Under torchrun
-    the problems are split over the ranks by cost (N^2 (nev + nex)), with no
-    collective on the data path; the time is the slowest rank's."""
+    """Standalone batched warm-start sequence (C5); see batch_leg."""
     import torch
 
     import paper_2309_15595_gb300 as lib
-    from synth import Problem, complex_normal
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -815,69 +962,9 @@ def run_batch(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    nprob, nsteps = args.batch_problems, args.batch_steps
-    Ns = batch_sizes(nprob)
-    costs = [float(N) ** 2 * (-(-N // 20) - (-N // 40)) for N in Ns]
-    mine = shard_problems(costs, world)[rank]
-    probs = [Problem(N=Ns[k], nev=-(-Ns[k] // 20), nex=-(-Ns[k] // 40), spectrum="uniform",
-                     lo=0.0, hi=10.0, reflectors=8, seed=1000 + k) for k in mine]
-    As = [p.matrix_torch(dev) for p in probs]
-    streams = [torch.cuda.Stream(dev) for _ in probs]
-    ctxs = [lib.Context(lib.default_params(p.N, p.nev, p.nex, precision=lib.CHASE_MIXED_BF16X3,
-                                           fp64_tensor=args.fp64_tensor), s)
-            for p, s in zip(probs, streams)]
-    Vs = [lib.colmajor(torch.from_numpy(p.start_block()).to(dev)) for p in probs]
-    rz = [torch.zeros(p.ne, dtype=torch.float64, device=dev) for p in probs]
-    rs = [torch.zeros_like(r) for r in rz]
-
-    def perturb(t):
-        for k, p, A in zip(mine, probs, As):
-            Z = torch.from_numpy(complex_normal(2000 + k, 100 + t, p.N * p.N)
-                                 .reshape(p.N, p.N)).to(dev)
-            E = 0.5 * (Z + Z.conj().T)
-            # ||E||_2 by 40 power steps on E^2 (input generation, not the method)
-            x = torch.ones(p.N, 1, dtype=E.dtype, device=dev)
-            for _ in range(40):
-                x = E @ (E @ x)
-                x /= torch.linalg.vector_norm(x)
-            E /= torch.linalg.vector_norm(E @ x)
-            A.add_(1e-3 * E)  # elementwise on the logical matrix (A keeps its strides)
-
-    step_ms, iters, mvs = [], [], []
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    for t in range(nsteps):
-        if t > 0:
-            perturb(t)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stats, status = lib.solve_batch(ctxs, As, Vs, rz, rs, threads=args.batch_threads,
-                                        allow_not_converged=True)
-        for s in streams:
-            torch.cuda.current_stream().wait_stream(s)
-        e1.record()
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        iters.append(sum(st["iters"] for st in stats))
-        mvs.append(sum(st["matvecs"] for st in stats))
-    clk = clocks.stop()
-    for cx in ctxs:
-        cx.close()
-    # whole job: all problems, the slowest rank's time (no collective on the data path)
-    _, total_ms, world = aggregate_over_ranks(sum(step_ms), 1, dist, dev)
-    total = total_ms / 1000.0
-    line = {"metric": METRIC, "kind": "batched warm-start sequence",
-            "value": nprob * nsteps / total, "unit": "solves/s", "higher_is_better": True,
-            "n_gpus": world, "scaling": "strong",
-            "config": {"workload": f"C5: {nprob} problems, N uniform in [256, 4096], nev = "
-                                   f"ceil(N/20), nex = ceil(N/40), {nsteps} steps A += 1e-3 E, "
-                                   "warm starts, mixed filter",
-                       "threads": args.batch_threads, "fp64_tensor": args.fp64_tensor,
-                       "parallelism": "problems split over ranks by cost" if world > 1
-                                      else "single GPU"},
-            "total_s": total, "step_ms_rank0": step_ms, "iterations_per_step_rank0": iters,
-            "matvecs_per_step_rank0": mvs, "clocks": clk, "data": "synthetic"}
+    res = batch_leg(lib, torch, dev, args.batch_problems, args.batch_steps, args.batch_threads,
+                    args.fp64_tensor, rank, world, dist)
+    line = {"metric": METRIC, "kind": "batched warm-start sequence", **res, "data": "synthetic"}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
