@@ -885,7 +885,7 @@ def batch_leg(lib, torch, dev, nprob, nsteps, threads, fp64_tensor, rank=0, worl
     rz = [torch.zeros(p.ne, dtype=torch.float64, device=dev) for p in probs]
     rs = [torch.zeros_like(r) for r in rz]
 
-    step_ms, iters, mvs, launches, not_conv = [], [], [], [], 0
+    step_ms, iters, mvs, launches, not_conv, phase_sum = [], [], [], [], 0, {}
     eig_err = 0.0
     clocks = ClockSampler(dev.index)
     clocks.start()
@@ -908,6 +908,8 @@ def batch_leg(lib, torch, dev, nprob, nsteps, threads, fp64_tensor, rank=0, worl
         iters.append(sum(st["iters"] for st in stats))
         mvs.append(sum(st["matvecs"] for st in stats))
         launches.append(sum(st["kernel_launches"] for st in stats))
+        for k in PHASES:
+            phase_sum[k] = phase_sum.get(k, 0.0) + sum(st[k] for st in stats)
         not_conv += sum(1 for s in status if s != 0)
         if t == 0:
             for p, r in zip(probs, rz):
@@ -937,6 +939,10 @@ def batch_leg(lib, torch, dev, nprob, nsteps, threads, fp64_tensor, rank=0, worl
             "total_s": total, "step_ms_rank0": step_ms, "iterations_per_step_rank0": iters,
             "matvecs_per_step_rank0": mvs, "gpu_launches_per_step_rank0": launches,
             "not_converged_rank0": not_conv,
+            "phase_ms_summed_over_problems_rank0": phase_sum,
+            "phase_note": "each problem's phase times on its own stream, summed over problems "
+                          "and steps; phases of different problems overlap on the GPU, and a "
+                          "grouped filter launch is charged to every problem of its group",
             "max_rel_eig_err_step0_rank0": eig_err,
             "max_rel_resid_recomputed_last_step_rank0": res_worst,
             "checks": "step 0 eigenvalues vs the exact spectra; last step residuals of all "

@@ -8,11 +8,14 @@
 // own context and stream (so small problems overlap on the GPU); the filter
 // phase of all problems that are in the reduced-precision mode (and live on
 // one device) runs as one CUDA graph of grouped tensor-core launches, one
-// launch per degree step covering every such problem's tiles. Problems in the
-// FP64 mode filter with their own launches. Each problem's arithmetic, and so
-// its results, are those of chase_solve on it alone: the grouped launch runs
-// every tile exactly as the per-problem launch does, and every reduction has a
-// fixed order.
+// launch per degree step covering every such problem's tiles, and so does the
+// filter phase of all problems in the FP64 mode with the tensor-core FP64
+// products (per degree step one launch slicing every problem's operand
+// columns into digits and one product launch). Problems in the FP64 mode with
+// the CUDA-core products filter with their own launches. Each problem's
+// arithmetic, and so its results, are those of chase_solve on it alone: the
+// grouped launches run every tile and column exactly as the per-problem
+// launches do, and every reduction has a fixed order.
 #include <algorithm>
 #include <atomic>
 #include <map>
@@ -101,6 +104,50 @@ int grouped_filter(int device, cudaStream_t s, const std::vector<int64_t>& idx,
   return CHASE_OK;
 }
 
+// The grouped filter phase of the problems in idx (all on `device`, all in the
+// FP64 mode with the tensor-core products) on the batch stream s.
+int grouped_fp64_filter(int device, cudaStream_t s, const std::vector<int64_t>& idx,
+                        std::vector<std::unique_ptr<SolveState>>& S, chase::OzakiGroupTable& tab) {
+  if (cudaSetDevice(device) != cudaSuccess) return CHASE_CUDA_FAIL();
+  const size_t n = idx.size();
+  std::vector<std::vector<double>> al(n), be(n);
+  std::vector<chase::OzakiGroupItem> items(n);
+  for (size_t i = 0; i < n; ++i) {
+    SolveState& st = *S[idx[i]];
+    chase_ctx* c = st.c;
+    if (!c->oz_a_valid) return CHASE_ERR_INVALID_ARG;  // A's digits come with solve_begin
+    const int64_t nact = c->ne - st.locked;
+    const int32_t* degs = st.degs.data() + st.locked;
+    chase::cheb_coefficients(degs[nact - 1], st.cc, st.ee, st.mu_1, c->p.scaled_filter != 0, al[i],
+                             be[i]);
+    items[i] = chase::OzakiGroupItem{c->N, st.C + st.locked * st.ldv, st.ldv, c->W, c->N, nact,
+                                     degs, st.cc, al[i].data(), be[i].data(), &c->ow};
+  }
+  if (chase::ozaki_group_reserve(tab, chase::ozaki_group_entries((int)n, items.data())) !=
+      cudaSuccess)
+    return CHASE_ERR_OOM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return CHASE_CUDA_FAIL();
+  cudaEventRecord(e0, s);
+  const long long l0 = chase::launch_count();
+  const int rc = chase::ozaki_filter_grouped(s, (int)n, items.data(), tab, nullptr);
+  const long long nl = chase::launch_count() - l0;
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CHASE_OK) return rc;
+  for (size_t i = 0; i < n; ++i) {
+    SolveState& st = *S[idx[i]];
+    st.st.ms_filter += ms;
+    st.launches += nl;
+    chase::solve_count_filter(st);
+  }
+  return CHASE_OK;
+}
+
 }  // namespace
 
 extern "C" int chase_solve_batch(int64_t count, chase_ctx* const* ctxs, const chase_c128* const* A,
@@ -140,6 +187,7 @@ extern "C" int chase_solve_batch(int64_t count, chase_ctx* const* ctxs, const ch
   });
   std::map<int, cudaStream_t> batch_stream;  // one per device holding grouped problems
   std::map<int, chase::MixedGroupTable> tables;
+  std::map<int, chase::OzakiGroupTable> oz_tables;
   auto alive = [&]() {
     std::vector<int64_t> a;
     for (int64_t k : order)
@@ -148,11 +196,13 @@ extern "C" int chase_solve_batch(int64_t count, chase_ctx* const* ctxs, const ch
   };
   for (std::vector<int64_t> act = alive(); !act.empty(); act = alive()) {
     run_parallel(act, nt, ctxs, status, [&](int64_t k) { status[k] = chase::solve_prepare(*S[k]); });
-    std::map<int, std::vector<int64_t>> grouped;
+    // groups per (device, precision tier): reduced precision, FP64 on the tensor cores
+    std::map<std::pair<int, int>, std::vector<int64_t>> grouped;
     std::vector<int64_t> own;
     for (int64_t k : act) {
       if (status[k] != CHASE_OK) continue;
-      if (S[k]->mixed) grouped[ctxs[k]->device].push_back(k);
+      if (S[k]->mixed) grouped[{ctxs[k]->device, 0}].push_back(k);
+      else if (ctxs[k]->p.fp64_tensor) grouped[{ctxs[k]->device, 1}].push_back(k);
       else own.push_back(k);
     }
     for (auto& g : grouped) {
@@ -160,15 +210,18 @@ extern "C" int chase_solve_batch(int64_t count, chase_ctx* const* ctxs, const ch
         own.push_back(g.second[0]);
         continue;
       }
-      cudaStream_t& bs = batch_stream[g.first];
+      const int dev = g.first.first;
+      cudaStream_t& bs = batch_stream[dev];
       if (!bs) {
-        if (cudaSetDevice(g.first) != cudaSuccess ||
+        if (cudaSetDevice(dev) != cudaSuccess ||
             cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) {
           for (int64_t k : g.second) status[k] = CHASE_ERR_CUDA;
           continue;
         }
       }
-      const int rc = grouped_filter(g.first, bs, g.second, S, tables[g.first]);
+      const int rc = g.first.second == 0
+                         ? grouped_filter(dev, bs, g.second, S, tables[dev])
+                         : grouped_fp64_filter(dev, bs, g.second, S, oz_tables[dev]);
       if (rc != CHASE_OK)
         for (int64_t k : g.second) status[k] = rc;
     }
@@ -191,6 +244,10 @@ extern "C" int chase_solve_batch(int64_t count, chase_ctx* const* ctxs, const ch
   for (auto& t : tables) {
     cudaSetDevice(t.first);
     chase::mixed_group_free(t.second);
+  }
+  for (auto& t : oz_tables) {
+    cudaSetDevice(t.first);
+    chase::ozaki_group_free(t.second);
   }
   S.clear();
   cudaSetDevice(dev0);

@@ -45,8 +45,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <type_traits>
 #include <cstdio>
+#include <type_traits>
+#include <vector>
 
 #include "ozaki.cuh"
 
@@ -67,6 +68,7 @@ constexpr int KPAD = 128;                // K-half padding: 2 Np is a multiple o
 constexpr int HC = TN / 4;               // complex columns per epilogue warp half (16)
 constexpr int CT = TN / 2;               // complex columns per tile (32)
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+constexpr unsigned kGroup = 8;           // row blocks per sweep of the column tiles
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,10 +186,13 @@ struct Params {
 };
 
 // ---------------------------------------------------------------- kernel
+// One 128 x 64 output tile (row block rb, column tile ct of the active
+// columns); the per-problem kernel and the grouped kernel (the filter steps
+// of many problems in one launch) both run it.
 template <int LMAX>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      Params P) {
+__device__ __forceinline__ void ozaki_tile(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                           const Params& P, unsigned rb, unsigned ct,
+                                           bool maps_in_global) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -196,8 +201,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
-  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, 8, rb, ct);
   const int64_t m0 = (int64_t)rb * TM;
   const int64_t tile = P.j0 / CT + ct;            // absolute CT-column tile
   const int nkb = (int)((2 * P.Np) / TK);
@@ -227,6 +230,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ------------------------------------ TMA producer
+      if (maps_in_global) {  // tensor maps read from global memory by the TMA unit
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA)
+                     : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB)
+                     : "memory");
+      }
       int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES;
@@ -243,11 +252,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int d = 0; d < OS; ++d) {
           // digit planes are stacked along rows: digit d of row r is row d * rows + r
-          tma_load_2d(smem_u32(st + d * A_TILE), &tmA, kx, (int)(d * P.arows + m0), full);
+          tma_load_2d(smem_u32(st + d * A_TILE), tmA, kx, (int)(d * P.arows + m0), full);
         }
 #pragma unroll
         for (int d = 0; d < OS; ++d) {
-          tma_load_2d(smem_u32(st + OS * A_TILE + d * B_TILE), &tmB, kx,
+          tma_load_2d(smem_u32(st + OS * A_TILE + d * B_TILE), tmB, kx,
                       (int)(d * P.brows + tile * TN), full);
         }
         ++issued;
@@ -429,6 +438,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+template <int LMAX>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      Params P) {
+  unsigned rb, ct;  // row block and column tile of this CTA (grouped raster order)
+  grouped_tile(blockIdx.x + blockIdx.y * gridDim.x, gridDim.x, gridDim.y, kGroup, rb, ct);
+  ozaki_tile<LMAX>(&tmA, &tmB, P, rb, ct, false);
+}
+
+// Many problems' filter steps in one launch: entry p of the table holds problem
+// p's tensor maps, step parameters and first CTA index; CTA id finds its
+// problem (binary search on the first indices) and runs that problem's tile
+// id - first in the raster order of the per-problem launch, so each problem's
+// result is that of its own launch.
+struct OzGroupEntry {  // aligned as its tensor maps
+  CUtensorMap a, b;
+  Params P;
+  int first, nrow, ncol, pad;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ozaki_filter_grouped_kernel(const OzGroupEntry* __restrict__ tab, int count) {
+  const int id = (int)blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last entry with first <= id
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].first <= id) lo = mid;
+    else hi = mid - 1;
+  }
+  const OzGroupEntry* e = tab + lo;
+  const Params P = e->P;
+  unsigned rb, ct;
+  grouped_tile((unsigned)(id - e->first), (unsigned)e->nrow, (unsigned)e->ncol, kGroup, rb, ct);
+  ozaki_tile<7>(&e->a, &e->b, P, rb, ct, true);
+}
+
 // ------------------------------------------------------------ digit prep
 __device__ __forceinline__ void digits_of(double x, __nv_bfloat16* d) {
   // |x| < 1/2: x = sum_s d_s 2^-8s + r, |d_s| <= 128 (exact in FP64 and BF16)
@@ -596,6 +641,69 @@ __global__ void slice_b_kernel(int64_t N, int64_t Np, int64_t brows, int64_t j0,
   }
 }
 
+// The right-operand digits of many problems' filter steps in one launch: one
+// CTA (256 threads) per active column of every problem. It forms the column's
+// maximum with the reduction of colexp_kernel, then the column's digits as
+// slice_b_kernel does, so each problem's planes are those of its own launches.
+struct OzSliceEntry {
+  const double2* B;          // right operand (absolute columns, ld ldb)
+  int64_t ldb, N, Np, brows, j0;
+  int* eb;                   // column exponents
+  __nv_bfloat16* out;        // digit planes
+  int first, pad;            // first CTA of this problem
+};
+
+__global__ void __launch_bounds__(256)
+    slice_b_grouped_kernel(const OzSliceEntry* __restrict__ tab, int count) {
+  __shared__ double red[256];
+  __shared__ int s_e;
+  const int id = (int)blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last entry with first <= id
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].first <= id) lo = mid;
+    else hi = mid - 1;
+  }
+  const OzSliceEntry& e = tab[lo];
+  const int64_t N = e.N, j = e.j0 + (id - e.first);
+  const double2* __restrict__ Y = e.B + j * e.ldb;
+  double m = 0.0;
+  for (int64_t k = threadIdx.x; k < N; k += 256) {
+    const double2 y = Y[k];
+    m = fmax(m, fmax(fabs(y.x), fabs(y.y)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    s_e = scale_exp(red[0]);
+    e.eb[j] = s_e;
+  }
+  __syncthreads();
+  const double sc = ldexp(1.0, -s_e);
+  const int64_t ld = 2 * e.Np;
+  const size_t plane = (size_t)e.brows * ld;
+  const int64_t br = brow_re(j), bi = br + CT;
+  for (int64_t k = threadIdx.x; k < N; k += 256) {
+    const double2 y = Y[k];
+    __nv_bfloat16 dr[OS], di[OS];
+    digits_of(y.x * sc, dr);
+    digits_of(y.y * sc, di);
+#pragma unroll
+    for (int d = 0; d < OS; ++d) {
+      __nv_bfloat16* o = e.out + d * plane;
+      const __nv_bfloat16 ndi = __hneg(di[d]);
+      o[br * ld + k] = dr[d];
+      o[br * ld + e.Np + k] = ndi;
+      o[bi * ld + k] = di[d];
+      o[bi * ld + e.Np + k] = dr[d];
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
   cudaDriverEntryPointQueryResult q;
@@ -625,6 +733,35 @@ bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows
 struct Maps {
   CUtensorMap a, b;
 };
+
+// Launch parameters of A * B[:, j0:ncols_end] with epilogue ep (A's digits in w).
+Params product_params(const OzakiWork& w, int64_t ncols_end, int64_t j0, const double2* B,
+                      int64_t ldb, const Epilogue& ep) {
+  Params P;
+  P.N = w.N;
+  P.Np = w.Np;
+  P.brows = w.brows;
+  P.arows = w.N;
+  P.j0 = j0;
+  P.ncols = ncols_end;
+  P.escale_a = w.ea;
+  P.escale_b = w.eb;
+  P.diag = w.diag;
+  P.Bsrc = B;
+  P.ldbs = ldb;
+  P.mode = ep.mode;
+  P.alpha = ep.alpha;
+  P.beta = ep.beta;
+  P.gamma = ep.gamma;
+  P.X = ep.X;
+  P.ldx = ep.ldx;
+  P.Y = ep.Y;
+  P.ldy = ep.ldy;
+  P.theta = ep.theta;
+  P.partial = ep.partial;
+  P.err = w.err;
+  return P;
+}
 
 }  // namespace
 
@@ -707,29 +844,7 @@ cudaError_t ozaki_gemm(cudaStream_t s, int64_t ncols_end, int64_t j0, const doub
       N, w.Np, w.brows, j0, B, ldb, w.eb, static_cast<__nv_bfloat16*>(w.Bd));
   count_launch();
   const Maps* maps = static_cast<const Maps*>(w.maps);
-  Params P;
-  P.N = N;
-  P.Np = w.Np;
-  P.brows = w.brows;
-  P.arows = N;
-  P.j0 = j0;
-  P.ncols = ncols_end;
-  P.escale_a = w.ea;
-  P.escale_b = w.eb;
-  P.diag = w.diag;
-  P.Bsrc = B;
-  P.ldbs = ldb;
-  P.mode = ep.mode;
-  P.alpha = ep.alpha;
-  P.beta = ep.beta;
-  P.gamma = ep.gamma;
-  P.X = ep.X;
-  P.ldx = ep.ldx;
-  P.Y = ep.Y;
-  P.ldy = ep.ldy;
-  P.theta = ep.theta;
-  P.partial = ep.partial;
-  P.err = w.err;
+  const Params P = product_params(w, ncols_end, j0, B, ldb, ep);
   const dim3 grid((unsigned)cdiv(N, TM), (unsigned)((ncols_end - 1) / CT - j0 / CT + 1), 1);
   ozaki_gemm_kernel<7><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps->a, maps->b, P);
   count_launch();
@@ -849,6 +964,147 @@ cudaError_t ozaki_left_exp_max(cudaStream_t s, int64_t M, OzakiWork& w, int* out
   exp_max_kernel<<<1, 256, 0, s>>>(M, w.el, out);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t ozaki_group_reserve(OzakiGroupTable& t, size_t entries) {
+  if (entries <= t.capacity) return cudaSuccess;
+  ozaki_group_free(t);
+  cudaError_t e;
+  if ((e = cudaMalloc(&t.dev, entries * sizeof(OzGroupEntry))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&t.host, entries * sizeof(OzGroupEntry))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.sdev, entries * sizeof(OzSliceEntry))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&t.shost, entries * sizeof(OzSliceEntry))) != cudaSuccess) return e;
+  t.capacity = entries;
+  return cudaSuccess;
+}
+
+void ozaki_group_free(OzakiGroupTable& t) {
+  if (t.dev) cudaFree(t.dev);
+  if (t.host) cudaFreeHost(t.host);
+  if (t.sdev) cudaFree(t.sdev);
+  if (t.shost) cudaFreeHost(t.shost);
+  t = OzakiGroupTable{};
+}
+
+size_t ozaki_group_entries(int count, const OzakiGroupItem* items) {
+  size_t n = 0;
+  for (int k = 0; k < count; ++k)
+    if (items[k].ncols > 0) n += (size_t)items[k].degs[items[k].ncols - 1];
+  return n;
+}
+
+int ozaki_filter_grouped(cudaStream_t s, int count, const OzakiGroupItem* items,
+                         OzakiGroupTable& t, int* launches) {
+  static std::once_flag attr_once[kMaxDevices];
+  once_per_device(attr_once, []() {
+    cudaFuncSetAttribute(ozaki_filter_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM_BYTES);
+  });
+  int dmax_all = 0;
+  for (int k = 0; k < count; ++k) {
+    const OzakiGroupItem& it = items[k];
+    if (it.ncols == 0) continue;
+    if (!it.w || !it.w->maps || !it.w->A_ready || it.N != it.w->N || it.ncols > it.w->ne ||
+        !it.V || !it.W || it.ldv < it.N || it.ldw < it.N)
+      return CHASE_ERR_INVALID_ARG;
+    dmax_all = std::max(dmax_all, (int)it.degs[it.ncols - 1]);
+  }
+  if (dmax_all == 0) return CHASE_OK;
+  if (ozaki_group_entries(count, items) > t.capacity) return CHASE_ERR_INVALID_ARG;
+  // step table: for step i the entries of the problems still filtering, with
+  // their first CTA indices (gemm) and first column indices (digits)
+  OzGroupEntry* host = static_cast<OzGroupEntry*>(t.host);
+  OzSliceEntry* shost = static_cast<OzSliceEntry*>(t.shost);
+  std::vector<size_t> off(dmax_all + 2, 0);
+  std::vector<int> ctas(dmax_all + 1, 0), cols(dmax_all + 1, 0);
+  size_t n = 0;
+  for (int i = 1; i <= dmax_all; ++i) {
+    off[i] = n;
+    int first = 0, sfirst = 0;
+    for (int k = 0; k < count; ++k) {
+      const OzakiGroupItem& it = items[k];
+      if (it.ncols == 0 || it.degs[it.ncols - 1] < i) continue;
+      OzakiWork& w = *it.w;
+      // the per-problem filter's step i (Eq. 1): Y_d = al[i] (A - c I) Y_s + be[i] Y_d
+      const int64_t j0 = std::lower_bound(it.degs, it.degs + it.ncols, i) - it.degs;
+      double2* buf[2] = {it.V, it.W};
+      const int64_t ld[2] = {it.ldv, it.ldw};
+      const int sp = (i - 1) & 1, d = i & 1;
+      Epilogue ep{};
+      ep.mode = EPI_FILTER;
+      ep.alpha = it.al[i];
+      ep.beta = (i == 1) ? 0.0 : it.be[i];
+      ep.gamma = it.c;
+      ep.X = buf[sp];
+      ep.ldx = ld[sp];
+      ep.Y = buf[d];
+      ep.ldy = ld[d];
+      OzSliceEntry& se = shost[n];
+      se.B = buf[sp];
+      se.ldb = ld[sp];
+      se.N = it.N;
+      se.Np = w.Np;
+      se.brows = w.brows;
+      se.j0 = j0;
+      se.eb = w.eb;
+      se.out = static_cast<__nv_bfloat16*>(w.Bd);
+      se.first = sfirst;
+      se.pad = 0;
+      sfirst += (int)(it.ncols - j0);
+      OzGroupEntry& e = host[n];
+      const Maps* maps = static_cast<const Maps*>(w.maps);
+      e.a = maps->a;
+      e.b = maps->b;
+      e.P = product_params(w, it.ncols, j0, buf[sp], ld[sp], ep);
+      e.nrow = (int)cdiv(it.N, TM);
+      e.ncol = (int)((it.ncols - 1) / CT - j0 / CT + 1);
+      e.first = first;
+      e.pad = 0;
+      first += e.nrow * e.ncol;
+      ++n;
+    }
+    ctas[i] = first;
+    cols[i] = sfirst;
+  }
+  off[dmax_all + 1] = n;
+  if (cudaMemcpyAsync(t.dev, host, n * sizeof(OzGroupEntry), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(t.sdev, shost, n * sizeof(OzSliceEntry), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return CHASE_CUDA_FAIL();
+  // the degree steps of all problems as one CUDA graph: per step one grouped
+  // digit launch and one grouped product launch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return CHASE_CUDA_FAIL();
+  const OzGroupEntry* dev = static_cast<const OzGroupEntry*>(t.dev);
+  const OzSliceEntry* sdev = static_cast<const OzSliceEntry*>(t.sdev);
+  for (int i = 1; i <= dmax_all; ++i) {
+    const int cnt = (int)(off[i + 1] - off[i]);
+    slice_b_grouped_kernel<<<(unsigned)cols[i], 256, 0, s>>>(sdev + off[i], cnt);
+    count_launch();
+    ozaki_filter_grouped_kernel<<<(unsigned)ctas[i], NTHREADS, SMEM_BYTES, s>>>(dev + off[i],
+                                                                               cnt);
+    count_launch();
+  }
+  const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (ce != cudaSuccess || !graph) return CHASE_CUDA_FAIL();
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return CHASE_CUDA_FAIL();
+  const cudaError_t le = cudaGraphLaunch(exec, s);
+  const cudaError_t se = le == cudaSuccess ? cudaStreamSynchronize(s) : le;
+  cudaGraphExecDestroy(exec);
+  if (se != cudaSuccess) return CHASE_CUDA_FAIL();
+  if (launches) *launches = 2 * dmax_all;
+  int rc = CHASE_OK;
+  for (int k = 0; k < count; ++k)
+    if (items[k].ncols > 0) {
+      const int r = ozaki_check(s, *items[k].w);
+      if (rc == CHASE_OK) rc = r;
+    }
+  return rc;
 }
 
 int ozaki_check(cudaStream_t s, OzakiWork& w) {

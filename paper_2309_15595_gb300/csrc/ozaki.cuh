@@ -56,4 +56,42 @@ cudaError_t ozaki_left_exp_max(cudaStream_t s, int64_t M, OzakiWork& w, int* out
 // Reads and clears the device error flag; returns a chase_status.
 int ozaki_check(cudaStream_t s, OzakiWork& w);
 
+// One problem of a grouped FP64-accurate filter (several problems' filters in
+// the same kernel launches): Eq. 1 on V[:, 0:ncols] with W as the ping-pong
+// buffer, the steps the per-problem filter takes with ozaki_gemm. A's digits
+// must be in w (ozaki_prepare_a).
+struct OzakiGroupItem {
+  int64_t N;
+  double2* V;
+  int64_t ldv;
+  double2* W;
+  int64_t ldw;
+  int64_t ncols;
+  const int32_t* degs;  // host, even, ascending
+  double c;
+  const double* al;     // host, dmax + 1 coefficients (al[i], be[i] of step i)
+  const double* be;
+  OzakiWork* w;
+};
+// Per-step, per-problem launch entries (device + pinned host) of the product
+// and of the digit slicing.
+struct OzakiGroupTable {
+  void* dev = nullptr;
+  void* host = nullptr;
+  void* sdev = nullptr;
+  void* shost = nullptr;
+  size_t capacity = 0;  // entries of each
+};
+// Entries a grouped filter of these items needs (sum of their largest degrees).
+size_t ozaki_group_entries(int count, const OzakiGroupItem* items);
+cudaError_t ozaki_group_reserve(OzakiGroupTable& t, size_t entries);
+void ozaki_group_free(OzakiGroupTable& t);
+// All items' filters on stream s as one CUDA graph: per degree step i one
+// launch that slices the operand columns of every problem whose largest
+// degree is >= i and one product launch over all their tiles. Each problem's
+// result equals that of its own filter with ozaki_gemm, bit for bit.
+// Synchronises s. *launches (may be null) receives the number of launches.
+int ozaki_filter_grouped(cudaStream_t s, int count, const OzakiGroupItem* items,
+                         OzakiGroupTable& t, int* launches);
+
 }  // namespace chase

@@ -3,8 +3,10 @@ along a sequence of perturbed matrices (A_{t+1} = A_t + 1e-3 E_t, ||E_t||_2 = 1)
 
 The batch advances all problems through Alg. 2 in lockstep: their
 reduced-precision filter phases run as grouped tensor-core launches (one per
-degree step for all problems, captured in a CUDA graph), the other phases on
-each problem's own context and stream from a host thread pool. Every tile of a
+degree step for all problems, captured in a CUDA graph), and so do their FP64
+filter phases when the FP64 products are the tensor-core ones (per degree step
+one grouped digit-slicing launch and one grouped product launch); the other
+phases run on each problem's own context and stream from a host thread pool. Every tile of a
 grouped launch is computed exactly as in the problem's own launch and every
 reduction has a fixed order, so the batched results must equal the
 one-at-a-time results bit for bit. The tensor-core filter's raster order is
@@ -36,7 +38,7 @@ def unit_hermitian(N, seed):
     return E / np.abs(np.linalg.eigvalsh(E)).max()
 
 
-@pytest.mark.parametrize("tensor,precision", [(0, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("tensor,precision", [(0, 0), (1, 1), (0, 1), (1, 0)])
 def test_batch_equals_single_solves(lib, tensor, precision):
     sizes = [256, 700, 384, 1000, 300]
     probs = [batch_problem(N, 40 + k) for k, N in enumerate(sizes)]
