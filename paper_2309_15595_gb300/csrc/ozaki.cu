@@ -475,15 +475,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------------ digit prep
+// |x| < 1/2: x = sum_s d_s 2^-8s + r with |r| <= 2^-49 and integer digits
+// |d_s| <= 128 (exact in BF16). X = rint(x 2^48) (|X| <= 2^47) is written in
+// balanced base 256, the low digits in [-128, 127] and the leading one in
+// [-128, 128]; so sum_s d_s 2^-8s = X 2^-48 exactly. Integer arithmetic: the
+// FP64 pipe (1/64 of the FP32 rate on this part) does one multiply and one
+// conversion per value instead of a multiply, a rounding and a subtraction
+// per digit.
 __device__ __forceinline__ void digits_of(double x, __nv_bfloat16* d) {
-  // |x| < 1/2: x = sum_s d_s 2^-8s + r, |d_s| <= 128 (exact in FP64 and BF16)
+  long long X = __double2ll_rn(x * 0x1p48);
 #pragma unroll
-  for (int s = 0; s < OS; ++s) {
-    const double r = x * 256.0;
-    const double di = rint(r);
-    d[s] = __double2bfloat16(di);
-    x = r - di;
+  for (int s = OS - 1; s > 0; --s) {
+    const int low = (int)(((unsigned)X + 128u) & 255u) - 128;  // X mod 256, balanced
+    d[s] = __float2bfloat16_rn((float)low);
+    X = (X - low) >> 8;  // exact: X - low is a multiple of 256
   }
+  d[0] = __float2bfloat16_rn((float)X);
 }
 
 __device__ __forceinline__ int scale_exp(double mx) {
