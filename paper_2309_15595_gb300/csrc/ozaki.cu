@@ -711,7 +711,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
@@ -721,17 +720,19 @@ PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
     return nullptr;
   return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
-bool get_encoder() {  // thread-safe one-time lookup
+// The driver's tensor-map encoder, looked up once (thread-safe static
+// initialisation; contexts may be created from several host threads).
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encoder();
-  g_encode = fn;
-  return fn != nullptr;
+  return fn;
 }
+bool get_encoder() { return encoder() != nullptr; }
 bool make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Np, int box_rows) {
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * Np), (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(2 * Np * 2)};
   const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
-  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
