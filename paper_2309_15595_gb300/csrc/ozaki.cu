@@ -1,8 +1,10 @@
 // FP64-accurate complex GEMM on the BF16 tensor cores (error-free splitting in
 // the manner of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication and its
-// applications", Numer. Algorithms 59, 2012), used for the FP64 filter, the
-// Rayleigh-Ritz product A Q and the residual product A V.
+// applications", Numer. Algorithms 59, 2012), used for the FP64 filter (also
+// grouped over many problems for the batched sequence), the Lanczos block
+// product, the Rayleigh-Ritz products, the residual product A V and the
+// CholeskyQR products.
 //
 // Same planar real form as the mixed filter: W = [Ar | Ai] [[Yr, Yi], [-Yi, Yr]].
 // The diagonal of A is taken out of the digit planes and applied exactly in
@@ -10,8 +12,9 @@
 // entries, which keeps their relative precision when A is diagonally dominant.
 // Row i of the left operand is scaled by 2^-e_i and column j of the right one
 // by 2^-f_j so every entry x has |x| < 1/2, then cut into S = 6 signed 8-bit
-// digits, x = sum_s d_s 2^-8s + O(2^-48), |d_s| <= 128, computed exactly in
-// FP64; every digit is exact in BF16. The product keeps the 21 digit pairs
+// digits, x = sum_s d_s 2^-8s + r with |r| <= 2^-49 and |d_s| <= 128 (the
+// balanced base-256 digits of rint(x 2^48), in integer arithmetic); every digit
+// is exact in BF16. The product keeps the 21 digit pairs
 // (s, t) with s + t <= 7; pair (s, t) contributes at weight 2^-8(s+t).
 // Digit products are < 2^14 and exact; the FP32 tensor-memory accumulator of
 // one level L = s + t stays an exact integer over a chunk of 256 K values
