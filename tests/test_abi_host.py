@@ -96,3 +96,54 @@ def test_new_entry_points_reject_invalid_arguments_without_gpu(pkg):
     it = ctypes.c_int32(0)
     assert L.chase_eig_vjp(None, None, 1, None, 1, None, 1, 1, None, None, 1, None, 1, 1e-10,
                            100, ctypes.byref(it)) == INVALID
+
+
+def _prototypes():
+    """name -> number of parameters of every CHASE_API function in include/*.h"""
+    out = {}
+    for h in HEADERS:
+        txt = re.sub(r"/\*.*?\*/", " ", open(h).read(), flags=re.S)
+        for name, params in re.findall(r"CHASE_API\s+[\w\s\*]*?\b(chase_\w+)\s*\(([^;]*?)\)\s*;",
+                                       txt, flags=re.S):
+            params = params.strip()
+            out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(pkg):
+    protos = _prototypes()
+    assert set(protos) == set(pkg._lib.SIGNATURES)
+    for name, (_, args) in pkg._lib.SIGNATURES.items():
+        assert len(args) == protos[name], name
+
+
+def test_binding_structs_match_the_header_layout(pkg, tmp_path):
+    """sizeof and every field offset of chase_params and chase_stats as the C
+    compiler lays them out from include/chase.h, against the ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"chase_params": pkg._lib.ChaseParams, "chase_stats": pkg._lib.ChaseStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "chase.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
