@@ -234,14 +234,17 @@ CHASE_API int chase_residuals_noalloc(const chase_c128* A, int64_t lda, const ch
  * N^2 (nev + nex) first), so that small problems overlap on the GPU. The
  * filter phase of all problems in the reduced-precision mode on one device
  * runs as one CUDA graph of grouped tensor-core launches, one launch per
- * degree step covering every such problem's tiles; problems in the FP64 mode
- * filter with their own launches. The tensor-core filter's raster order is
+ * degree step covering every such problem's tiles; so does the filter phase of
+ * all problems in the FP64 mode with the tensor-core products (fp64_tensor),
+ * per degree step one grouped digit-slicing launch and one grouped product
+ * launch. Problems with the CUDA-core FP64 products filter with their own
+ * launches. The split-BF16x3 filter's raster order is
  * chosen per shape by timing on its first use (see chase_filter). Warm starts
  * (a sequence of related matrices, Section 1) pass the previous Ritz vectors
  * as V. The contexts must be distinct. This call creates one extra stream per
- * device that holds grouped problems and a small table of launch parameters
- * (device and pinned host memory, about 640 bytes per problem and degree
- * step), and frees both before returning. In stats, the grouped filter's time
+ * device that holds grouped problems and small tables of launch parameters
+ * (device and pinned host memory, under 1 KB per problem and degree step),
+ * and frees them before returning. In stats, the grouped filter's time
  * and launches are charged to every problem of the group. status[k] receives
  * each return code; the call returns CHASE_OK if all are CHASE_OK, else the
  * first non-OK status in problem order. The paper solves one problem at a
